@@ -1,0 +1,193 @@
+/*
+ * llp.h — C ABI of libllp.so, the single-GPU (sm_103a) lattice-linear
+ * predicate (LLP) sweep engine.
+ *
+ * Method (paper Sec. 3, Algorithm LLP): a problem is a state vector G, a
+ * predicate forbidden(G, j) and a monotone advance(G, j).  Starting from the
+ * bottom of the lattice, every forbidden index is advanced, in parallel and in
+ * any order, until no index is forbidden; the result is the least G that
+ * satisfies the problem's predicate.  Each entry point below is one problem of
+ * the paper's Sec. 4 run to that fixed point on the GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers are DEVICE pointers unless their name starts with h_.  The caller
+ *    owns every buffer; the library keeps no pointer after a call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls only enqueue work on it: no allocation, no host synchronisation.
+ *    Exception: llp_get_status() synchronises `stream`.
+ *  - Scratch memory comes from the caller's `ws` (`ws_bytes` long, 256-byte
+ *    aligned), sized by the matching *_workspace_size() query.  A workspace may
+ *    be reused by consecutive calls on one stream; two calls in flight at the
+ *    same time must not share one.
+ *  - The return value is the HOST-side status: argument validation and launch
+ *    errors (LLP_ERR_INVALID_ARG, LLP_ERR_WORKSPACE_TOO_SMALL, LLP_ERR_CUDA).
+ *    On a non-OK return nothing was enqueued (LLP_ERR_CUDA: possibly partly).
+ *  - DEVICE-side outcomes (LLP_ERR_TIMEOUT, LLP_ERR_INFEASIBLE,
+ *    LLP_ERR_OVERFLOW) are written to a status word in the workspace header;
+ *    read it with llp_get_status().  Every device-side wait (grid barrier,
+ *    work queue) is bounded by `deadline_ns`; when it expires the kernel stops
+ *    cleanly and reports LLP_ERR_TIMEOUT, outputs are then undefined.
+ *  - `sched` (may be NULL = built-in heuristic) only changes HOW the sweep
+ *    runs, never the result: every schedule reaches the same least fixed point.
+ *  - All results are integers and independent of scheduling, bit for bit.
+ */
+#ifndef LLP_H
+#define LLP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t llp_status_t;
+
+#define LLP_OK 0
+#define LLP_ERR_INVALID_ARG 1
+#define LLP_ERR_WORKSPACE_TOO_SMALL 2
+#define LLP_ERR_CUDA 3
+#define LLP_ERR_TIMEOUT 4
+#define LLP_ERR_INFEASIBLE 5 /* Algorithm LLP returns null: an advance passes the top T[j] */
+#define LLP_ERR_OVERFLOW 6
+#define LLP_ERR_UNSUPPORTED 7
+
+/* Sweep modes (llp_sched_t.mode). */
+#define LLP_MODE_AUTO 0   /* per sweep: dense when the worklist is large */
+#define LLP_MODE_SPARSE 1 /* always walk the worklist (paper's bag / shared work bag) */
+#define LLP_MODE_DENSE 2  /* always scan every index's "changed" stamp (paper's all-indices solver) */
+
+#define LLP_DELTA_INF 0xFFFFFFFFu /* no priority buckets: one worklist (Bellman-Ford order) */
+
+/* Compressed sparse rows of OUT-arcs.  offsets has n+1 entries, int32 if
+ * offsets_64 == 0 else int64, non-decreasing, offsets[0] == 0, offsets[n] == m;
+ * indices[m] are target vertices in [0, n); weights[m] (may be NULL where the
+ * problem ignores them).  Self-loops and parallel arcs are allowed. */
+typedef struct llp_csr {
+    int32_t n;
+    int32_t offsets_64;
+    int64_t m;
+    const void *offsets;
+    const int32_t *indices;
+    const uint32_t *weights;
+} llp_csr_t;
+
+/* Schedule.  Fields never change results.  Every field 0 = heuristic choice,
+ * so a zero-initialised struct (or sched == NULL) is the default schedule. */
+typedef struct llp_sched {
+    int32_t mode;           /* LLP_MODE_* (0 = AUTO) */
+    uint32_t delta;         /* SSSP/BFS priority-bucket width in distance units; 0 = auto,
+                               LLP_DELTA_INF = no buckets */
+    int32_t block_cfg;      /* work-block configuration 1..LLP_BLOCK_CFGS (see below); 0 = auto */
+    int32_t dense_permille; /* AUTO mode: dense sweep when worklist > n * dense_permille / 1000 (0 = 50) */
+    int32_t use_mlp;        /* 1: the learned scheduler model chooses mode, delta and block_cfg */
+    int32_t threads;        /* threads per CTA: 0 = auto, else 256 or 512 */
+    int64_t deadline_ns;    /* device wait limit of one call; 0 = default (10 s) */
+    const float *mlp_params;/* device pointer to the scheduler network's parameters when use_mlp = 1 */
+} llp_sched_t;
+
+/* Work-block configurations of the graph sweep: (small-vertex degree limit,
+ * arcs per chunk of a large vertex), selected by block_cfg:
+ *   1: (16, 128)   2: (32, 256)   3: (64, 512) */
+#define LLP_BLOCK_CFGS 3
+
+/* Device-side outcome and counters of the last call that used a workspace. */
+typedef struct llp_stats {
+    int32_t status;     /* LLP_OK or a device-side LLP_ERR_* */
+    int32_t sweeps;     /* forbidden/advance sweeps executed (grid barriers) */
+    int64_t items;      /* worklist items evaluated */
+    int64_t edges;      /* arcs / dependents examined by forbidden() */
+    int64_t advances;   /* successful advances (monotone updates that changed G) */
+    int64_t aux;        /* problem-specific: SSSP bucket advances, marriage proposals, ... */
+    int64_t elapsed_ns; /* device time of the sweep loop (%globaltimer) */
+    int32_t mode_used;  /* schedule actually used */
+    uint32_t delta_used;
+    int32_t block_cfg_used;
+    int32_t dense_sweeps; /* sweeps run in dense mode */
+} llp_stats_t;
+
+const char *llp_version(void);
+const char *llp_status_string(llp_status_t code);
+
+/* Synchronises `stream`, then copies the workspace header of the last call
+ * that used `ws` into *out.  Returns out->status, or LLP_ERR_CUDA. */
+llp_status_t llp_get_status(const void *ws, void *stream, llp_stats_t *out);
+
+/* ------------------------------------------------------------------ SSSP
+ * Paper Sec. 4.1: G[v] = d(v); v is forbidden iff some arc (u,v) has
+ * d(v) > d(u) + w(u,v); advance sets d(v) to the minimum over such arcs.
+ * Implemented push-style on out-arcs with atomicMin (the same least fixed
+ * point).  Result: dist[v] = length of a shortest path from `source`, or
+ * 0xFFFFFFFF if v is unreachable.  Path lengths are formed in 64 bits; a finite
+ * length >= 0xFFFFFFFF sets LLP_ERR_OVERFLOW (device status).
+ * dist: uint32[n], written in place (it is the state vector G). */
+size_t llp_sssp_workspace_size(int32_t n, int64_t m);
+llp_status_t llp_sssp(const llp_csr_t *g, int32_t source, uint32_t *dist, const llp_sched_t *sched,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------- BFS
+ * Paper Sec. 4.2: G[v] = level; v is forbidden iff an in-neighbour u has
+ * G[u] < G[v] - 1; advance sets G[v] = 1 + min G[u].  level[v] = hop distance
+ * from `source`, 0xFFFFFFFF if unreachable.  g->weights is ignored. */
+size_t llp_bfs_workspace_size(int32_t n, int64_t m);
+llp_status_t llp_bfs(const llp_csr_t *g, int32_t source, uint32_t *level, const llp_sched_t *sched,
+                     void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------- Stable marriage
+ * Paper Sec. 4.3: G[m] = index into man m's preference list; m is forbidden
+ * iff the woman he targets prefers another man who targets her; advance
+ * moves to his next choice.  The fixed point is the man-optimal stable
+ * matching.  men_pref[m*n + k] = k-th choice of man m; women_rank[w*n + m] =
+ * rank of m for woman w (0 = best; each row a permutation of 0..n-1).
+ * Outputs: wife[m]; husband[w] and next[m] (= G, the final list index) if not
+ * NULL.  A list exhausted (malformed input) gives LLP_ERR_INFEASIBLE.
+ * 1 <= n <= 2^24. */
+size_t llp_stable_marriage_workspace_size(int32_t n);
+llp_status_t llp_stable_marriage(int32_t n, const int32_t *men_pref, const int32_t *women_rank, int32_t *wife,
+                                 int32_t *husband, int32_t *next, const llp_sched_t *sched, void *ws,
+                                 size_t ws_bytes, void *stream);
+
+/* --------------------------------------------------------- 0-1 knapsack
+ * Paper Sec. 4.7: cell G[k,c] = best value of items 0..k-1 within capacity c;
+ * forbidden iff G[k,c] < max(G[k-1,c], v_k + G[k-1,c-w_k]); advance raises it
+ * to that bound.  best[0] = G[n, capacity]; final_row (optional, int32[capacity+1])
+ * = G[n, 0..capacity].  Requires w[i] >= 1, v[i] >= 0, sum(v) < 2^31,
+ * 0 <= capacity <= 2^26. */
+size_t llp_knapsack_workspace_size(int32_t n_items, int32_t capacity);
+llp_status_t llp_knapsack(int32_t n_items, const int32_t *w, const int32_t *v, int32_t capacity, int32_t *best,
+                          int32_t *final_row, const llp_sched_t *sched, void *ws, size_t ws_bytes, void *stream);
+
+/* --------------------------------------------------- Transitive closure
+ * Paper Sec. 4.6: G[u,v] boolean; (u,v) is forbidden iff not G[u,v] and
+ * G[u,w] and G[w,v] for some w; advance sets G[u,v].  reach: n rows of
+ * W = ceil(n/32) uint32 words; bit (v & 31) of reach[u*W + v/32] (least
+ * significant bit first) is 1 iff a path of >= 1 arcs leads from u to v.
+ * g->weights is ignored.  n <= 65536. */
+size_t llp_transitive_closure_workspace_size(int32_t n, int64_t m);
+llp_status_t llp_transitive_closure(const llp_csr_t *g, uint32_t *reach, const llp_sched_t *sched, void *ws,
+                                    size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------- Job scheduling
+ * Paper Sec. 4.4: G[j] = completion time, initially t_j; j is forbidden iff
+ * all predecessors are fixed and G[j] < max_p G[p] + t_j; advance raises it
+ * and fixes j.  completion[j] = t_j + max over predecessors (0 if none).
+ * succ: CSR of successor arcs (weights ignored).  duration[j] >= 0.
+ * A cycle leaves some job never ready: LLP_ERR_INFEASIBLE. */
+size_t llp_job_schedule_workspace_size(int32_t n, int64_t m);
+llp_status_t llp_job_schedule(const llp_csr_t *succ, const int32_t *duration, int32_t *completion,
+                              const llp_sched_t *sched, void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------ Reduction
+ * Paper Sec. 4.5: nodes of a reduction tree; a node is forbidden once all its
+ * children have published and it has not combined them.  sum[0] = sum of x
+ * modulo 2^64.  n >= 0. */
+size_t llp_reduce_workspace_size(int64_t n);
+llp_status_t llp_reduce(int64_t n, const uint64_t *x, uint64_t *sum, const llp_sched_t *sched, void *ws,
+                        size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LLP_H */

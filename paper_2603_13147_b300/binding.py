@@ -1,0 +1,203 @@
+"""Thin ctypes binding over libllp.so (include/llp.h).
+
+Argument marshalling only: torch tensors supply device memory and streams, every
+step of every sweep runs in the library's CUDA kernels.  There is no CPU
+fallback: if libllp.so is missing or no CUDA device is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libllp.so")
+
+LLP_OK = 0
+LLP_ERR_INVALID_ARG = 1
+LLP_ERR_WORKSPACE_TOO_SMALL = 2
+LLP_ERR_CUDA = 3
+LLP_ERR_TIMEOUT = 4
+LLP_ERR_INFEASIBLE = 5
+LLP_ERR_OVERFLOW = 6
+LLP_ERR_UNSUPPORTED = 7
+
+MODE_AUTO, MODE_SPARSE, MODE_DENSE = 0, 1, 2
+DELTA_INF = 0xFFFFFFFF
+INF = 0xFFFFFFFF
+
+
+class LlpError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+        self.code = code
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("offsets_64", ctypes.c_int32), ("m", ctypes.c_int64),
+                ("offsets", ctypes.c_void_p), ("indices", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
+
+
+class Sched(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("delta", ctypes.c_uint32), ("block_cfg", ctypes.c_int32),
+                ("dense_permille", ctypes.c_int32), ("use_mlp", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("deadline_ns", ctypes.c_int64), ("mlp_params", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("items", ctypes.c_int64),
+                ("edges", ctypes.c_int64), ("advances", ctypes.c_int64), ("aux", ctypes.c_int64),
+                ("elapsed_ns", ctypes.c_int64), ("mode_used", ctypes.c_int32), ("delta_used", ctypes.c_uint32),
+                ("block_cfg_used", ctypes.c_int32), ("dense_sweeps", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libllp.so; raises if it is missing (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libllp.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.llp_version.restype = ctypes.c_char_p
+        L.llp_status_string.restype = ctypes.c_char_p
+        for name in ("llp_sssp_workspace_size", "llp_bfs_workspace_size", "llp_stable_marriage_workspace_size",
+                     "llp_knapsack_workspace_size", "llp_transitive_closure_workspace_size",
+                     "llp_job_schedule_workspace_size", "llp_reduce_workspace_size"):
+            if hasattr(L, name):
+                getattr(L, name).restype = ctypes.c_size_t
+        _lib = L
+    return _lib
+
+
+def version() -> str:
+    return lib().llp_version().decode()
+
+
+def status_string(code: int) -> str:
+    return lib().llp_status_string(ctypes.c_int32(code)).decode()
+
+
+def make_sched(mode=0, delta=0, block_cfg=0, dense_permille=0, use_mlp=0, threads=0, deadline_ns=0,
+               mlp_params=None) -> Sched:
+    s = Sched()
+    s.mode, s.delta, s.block_cfg, s.dense_permille = mode, delta, block_cfg, dense_permille
+    s.use_mlp, s.threads, s.deadline_ns = use_mlp, threads, deadline_ns
+    s.mlp_params = None if mlp_params is None else mlp_params.data_ptr()
+    return s
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(rc, what):
+    if rc != LLP_OK:
+        raise LlpError(rc, what)
+
+
+def _dev(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """Device workspace (uint8, 256-byte aligned by the CUDA caching allocator)."""
+    return torch.empty(max(int(nbytes), 4096), dtype=torch.uint8, device=device or "cuda")
+
+
+def get_status(ws: torch.Tensor, stream=None) -> dict:
+    st = Stats()
+    rc = lib().llp_get_status(_ptr(ws), _stream(stream), ctypes.byref(st))
+    if rc == LLP_ERR_CUDA:
+        raise LlpError(rc, "llp_get_status")
+    return st.as_dict()
+
+
+# ------------------------------------------------------------------ graphs
+
+class DeviceGraph:
+    """A CSR graph resident on the device (out-arcs)."""
+
+    def __init__(self, offsets: torch.Tensor, indices: torch.Tensor, weights: torch.Tensor | None):
+        if offsets.dtype not in (torch.int32, torch.int64):
+            raise TypeError("offsets must be int32 or int64")
+        _dev(offsets, offsets.dtype, "offsets")
+        _dev(indices, torch.int32, "indices")
+        if weights is not None:
+            _dev(weights, torch.int32 if weights.dtype == torch.int32 else torch.uint32, "weights")
+        self.offsets, self.indices, self.weights = offsets, indices, weights
+        self.n = offsets.shape[0] - 1
+        self.m = indices.shape[0]
+
+    @classmethod
+    def from_host(cls, g: dict, device="cuda", offsets_64: bool = False):
+        import numpy as np
+        off = g["offsets"].astype(np.int64 if offsets_64 else np.int32)
+        w = g.get("weights")
+        return cls(torch.from_numpy(off).to(device), torch.from_numpy(g["indices"]).to(device),
+                   None if w is None else torch.from_numpy(w.view(np.int32)).to(device))
+
+    def csr(self) -> Csr:
+        c = Csr()
+        c.n, c.m = self.n, self.m
+        c.offsets_64 = 1 if self.offsets.dtype == torch.int64 else 0
+        c.offsets, c.indices = self.offsets.data_ptr(), self.indices.data_ptr()
+        c.weights = None if self.weights is None else self.weights.data_ptr()
+        return c
+
+
+def sssp_workspace_size(n: int, m: int) -> int:
+    return int(lib().llp_sssp_workspace_size(ctypes.c_int32(n), ctypes.c_int64(m)))
+
+
+def bfs_workspace_size(n: int, m: int) -> int:
+    return int(lib().llp_bfs_workspace_size(ctypes.c_int32(n), ctypes.c_int64(m)))
+
+
+def _graph_call(fn, wsfn, g: DeviceGraph, source, out, sched, ws, stream, what):
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.int32, device=g.indices.device)
+    _dev(out, torch.int32, "out")
+    if ws is None:
+        ws = workspace(wsfn(g.n, g.m), g.indices.device)
+    c = g.csr()
+    rc = fn(ctypes.byref(c), ctypes.c_int32(source), _ptr(out), None if sched is None else ctypes.byref(sched),
+            _ptr(ws), ctypes.c_size_t(ws.numel()), _stream(stream))
+    _check(rc, what)
+    return out, ws
+
+
+def sssp(g: DeviceGraph, source: int, out=None, sched: Sched | None = None, ws=None, stream=None):
+    """Shortest-path distances as int32 bit patterns of uint32 (0xFFFFFFFF = unreachable).
+    Returns (dist, workspace)."""
+    if g.weights is None:
+        raise ValueError("sssp needs weights")
+    return _graph_call(lib().llp_sssp, sssp_workspace_size, g, source, out, sched, ws, stream, "llp_sssp")
+
+
+def bfs(g: DeviceGraph, source: int, out=None, sched: Sched | None = None, ws=None, stream=None):
+    """BFS levels (uint32 bit patterns in int32; 0xFFFFFFFF = unreachable).  Returns (level, workspace)."""
+    return _graph_call(lib().llp_bfs, bfs_workspace_size, g, source, out, sched, ws, stream, "llp_bfs")
+
+
+def as_u32(t: torch.Tensor):
+    """View an int32 tensor holding uint32 bit patterns as a numpy uint32 array (host)."""
+    return t.cpu().numpy().view("uint32")

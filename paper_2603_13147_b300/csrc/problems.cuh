@@ -1,0 +1,126 @@
+// CTA-level LLP solvers shared by the single-instance entry points and the
+// batched engine.  Each routine solves one whole instance with the threads of
+// one CTA, sweeps separated by __syncthreads (a CTA-local barrier).
+#pragma once
+
+#include "llp_common.cuh"
+
+namespace llp {
+
+constexpr unsigned long long kEmptySuitor = 0xFFFFFFFFFFFFFFFFull;
+
+// ------------------------------------------------------------ stable marriage
+// Paper Sec. 4.3.  G[m] = next[m], the index into man m's list.  m is
+// forbidden iff the woman w he targets holds a suitor she ranks better; the
+// predicate is evaluated in O(1) against best[w] = packed (rank << 32 | man)
+// minimum over every man that ever targeted w (the all-time best suitor is the
+// only one never forbidden at w, so "ever" equals "currently").  Advance moves m
+// to his next choice.  A thread carries one free man; when its man displaces
+// another, it continues with the displaced one (his advance follows at once),
+// so no sweep barrier is needed.  Returns the number of proposals.
+// `best` may live in shared or global memory (generic pointer); `next` too.
+__device__ __forceinline__ unsigned long long propose_chain(int32_t m, int32_t k, int32_t n, const int32_t *men_pref,
+                                                            const int32_t *women_rank,
+                                                            unsigned long long *best, int32_t *next,
+                                                            WsHeader *h, long long deadline, bool &failed) {
+    unsigned long long proposals = 0;
+    for (;;) {
+        if (k >= n) {  // list exhausted: Algorithm LLP's "null" (advance beyond T[m])
+            set_status(h, LLP_ERR_INFEASIBLE);
+            failed = true;
+            return proposals;
+        }
+        if ((proposals & 1023ull) == 1023ull && globaltimer_ns() > deadline) {
+            set_status(h, LLP_ERR_TIMEOUT);
+            failed = true;
+            return proposals;
+        }
+        const int32_t w = __ldg(men_pref + (int64_t)m * n + k);
+        const uint32_t r = (uint32_t)__ldg(women_rank + (int64_t)w * n + m);
+        const unsigned long long mine = ((unsigned long long)r << 32) | (uint32_t)m;
+        proposals++;
+        // forbidden check without an atomic: w already holds a better suitor
+        const unsigned long long cur = *(volatile unsigned long long *)(best + w);
+        if (cur < mine) {
+            k++;
+            continue;
+        }
+        next[m] = k;
+        __threadfence();
+        const unsigned long long old = atomicMin(best + w, mine);
+        if (old < mine) {  // lost the race: forbidden after all
+            k++;
+            continue;
+        }
+        if (old == kEmptySuitor) return proposals;  // w was free: chain ends
+        // m displaced old's man, who is forbidden now: carry him
+        __threadfence();
+        m = (int32_t)(uint32_t)(old & 0xFFFFFFFFull);
+        k = *(volatile int32_t *)(next + m) + 1;
+    }
+}
+
+// ------------------------------------------------------------------ knapsack
+// Paper Sec. 4.7.  Row `row` (W+1 int32 cells, shared or global memory) holds
+// G[k-1, *] before item k and G[k, *] after it.  Capacities are processed top
+// down in chunks of blockDim.x * R cells: every cell of a chunk computes
+// max(G[k-1,c], v_k + G[k-1,c-w_k]) into registers, the CTA synchronises, then
+// writes; cells below the chunk are still G[k-1, *] when read, so one buffer
+// suffices.  Returns false on overflow (sum of values >= 2^31).
+template <int R>
+__device__ __forceinline__ void knapsack_cta(int32_t n, const int32_t *w, const int32_t *v, int32_t W, int32_t *row) {
+    const int T = blockDim.x;
+    for (int32_t c = threadIdx.x; c <= W; c += T) row[c] = 0;
+    __syncthreads();
+    const int64_t chunk = (int64_t)T * R;
+    for (int32_t k = 0; k < n; k++) {
+        const int32_t wk = __ldg(w + k);
+        const int32_t vk = __ldg(v + k);
+        if (wk > W) continue;  // item never fits: row unchanged (uniform branch)
+        // chunks from the top; the lowest chunk may be partial
+        for (int64_t top = (int64_t)W + 1; top > wk; top -= chunk) {
+            const int64_t lo = top - chunk > wk ? top - chunk : (int64_t)wk;
+            int32_t nv[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int64_t c = lo + (int64_t)r * T + threadIdx.x;
+                nv[r] = 0;
+                if (c < top) {
+                    const int32_t keep = row[c];
+                    const int32_t take = row[c - wk] + vk;
+                    nv[r] = keep > take ? keep : take;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int64_t c = lo + (int64_t)r * T + threadIdx.x;
+                if (c < top) row[c] = nv[r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Sum of values (int64) by the CTA; used to reject instances whose optimum can
+// overflow int32 before sweeping.
+__device__ __forceinline__ long long cta_sum_i32(int32_t n, const int32_t *v) {
+    __shared__ long long s_part[32];
+    long long acc = 0;
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) acc += __ldg(v + i);
+    acc = warp_sum(acc);
+    if (lane_id() == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    long long tot = 0;
+    if (threadIdx.x < 32) {
+        tot = (threadIdx.x < (blockDim.x >> 5)) ? s_part[threadIdx.x] : 0;
+        tot = warp_sum(tot);
+        if (threadIdx.x == 0) s_part[0] = tot;
+    }
+    __syncthreads();
+    tot = s_part[0];
+    __syncthreads();
+    return tot;
+}
+
+}  // namespace llp

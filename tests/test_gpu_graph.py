@@ -1,0 +1,179 @@
+"""GPU parity of llp_sssp / llp_bfs (through the C ABI) against the oracle, bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import read_golden
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def llp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2603_13147_b300 as m
+    m.lib()
+    return m
+
+
+def dev_graph(llp, g, offsets_64=False):
+    return llp.DeviceGraph.from_host(g, "cuda", offsets_64=offsets_64)
+
+
+def run_sssp(llp, g, s, **kw):
+    dg = dev_graph(llp, g, kw.pop("offsets_64", False))
+    sched = llp.make_sched(**kw) if kw else None
+    d, ws = llp.sssp(dg, s, sched=sched)
+    st = llp.get_status(ws)
+    assert st["status"] == 0, st
+    return llp.as_u32(d), st
+
+
+def run_bfs(llp, g, s, **kw):
+    dg = dev_graph(llp, g, kw.pop("offsets_64", False))
+    sched = llp.make_sched(**kw) if kw else None
+    d, ws = llp.bfs(dg, s, sched=sched)
+    st = llp.get_status(ws)
+    assert st["status"] == 0, st
+    return llp.as_u32(d), st
+
+
+def csr_from_arcs(n, arcs):
+    arcs = sorted(enumerate(arcs), key=lambda t: (t[1][0], t[0]))
+    off = np.zeros(n + 1, np.int64)
+    for _, a in arcs:
+        off[a[0] + 1] += 1
+    return dict(n=n, m=len(arcs), offsets=np.cumsum(off), indices=np.array([a[1] for _, a in arcs], np.int32),
+                weights=np.array([a[2] for _, a in arcs], np.uint32))
+
+
+SCHEDS = [dict(), dict(mode=1), dict(mode=2), dict(mode=1, delta=64), dict(mode=0, delta=8, block_cfg=1),
+          dict(mode=2, delta=300, block_cfg=3, threads=256), dict(delta=1, block_cfg=1)]
+
+
+def test_paper_example(llp):
+    gd = read_golden("sssp_paper_example.txt")
+    n = int(gd["n"][0])
+    g = csr_from_arcs(n, [tuple(int(x) for x in a.split()) for a in gd["arc"]])
+    for kw in SCHEDS:
+        d, _ = run_sssp(llp, g, 0, **kw)
+        assert d.tolist() == [int(x) for x in gd["final"][0].split()]
+
+
+@pytest.mark.parametrize("kw", SCHEDS)
+def test_sssp_er16k_all_schedules(llp, kw):
+    g = synth.er16k()
+    ref = oracle.sssp(g["offsets"], g["indices"], g["weights"], 0)
+    d, st = run_sssp(llp, g, 0, **kw)
+    assert (d == ref).all()
+    assert st["advances"] >= int((ref != oracle.INF).sum()) - 1
+
+
+@pytest.mark.parametrize("kw", SCHEDS[:4])
+def test_bfs_er16k(llp, kw):
+    g = synth.er16k()
+    ref = oracle.bfs(g["offsets"], g["indices"], 0)
+    d, _ = run_bfs(llp, g, 0, **kw)
+    assert (d == ref).all()
+
+
+def test_chain_many_sweeps(llp):
+    n = 3000
+    g = csr_from_arcs(n, [(i, i + 1, 1 + (i % 7)) for i in range(n - 1)])
+    ref = oracle.sssp(g["offsets"], g["indices"], g["weights"], 0)
+    d, st = run_sssp(llp, g, 0)
+    assert (d == ref).all()
+    assert st["sweeps"] >= n - 1  # one vertex becomes forbidden per sweep
+    assert st["items"] == n - 1   # informed selection: O(n) work (the paper's chain claim)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_small_and_ragged(llp, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 3000))
+    m = int(rng.integers(0, 6 * n))
+    arcs = [(int(rng.integers(n)), int(rng.integers(n)), int(rng.integers(1, 1000))) for _ in range(m)]
+    # a few hubs to exercise the chunk path
+    for h in range(min(3, n)):
+        arcs += [(h, int(rng.integers(n)), int(rng.integers(1, 50))) for _ in range(int(rng.integers(0, 1500)))]
+    g = csr_from_arcs(n, arcs)
+    s = int(rng.integers(n))
+    ref = oracle.sssp(g["offsets"], g["indices"], g["weights"], s)
+    for kw in SCHEDS[::2]:
+        d, _ = run_sssp(llp, g, s, offsets_64=bool(seed % 2), **kw)
+        assert (d == ref).all(), kw
+    refb = oracle.bfs(g["offsets"], g["indices"], s)
+    d, _ = run_bfs(llp, g, s)
+    assert (d == refb).all()
+
+
+def test_edge_cases(llp):
+    # single vertex, no arcs
+    g = dict(n=1, m=0, offsets=np.zeros(2, np.int64), indices=np.zeros(0, np.int32), weights=np.zeros(0, np.uint32))
+    d, st = run_sssp(llp, g, 0)
+    assert d.tolist() == [0]
+    # source without out-arcs
+    g = csr_from_arcs(5, [(1, 2, 3), (2, 3, 4)])
+    d, _ = run_sssp(llp, g, 0)
+    assert d.tolist() == [0] + [oracle.INF] * 4
+    # self loops and parallel arcs
+    g = csr_from_arcs(3, [(0, 0, 1), (0, 1, 9), (0, 1, 4), (1, 1, 2), (1, 2, 7), (1, 2, 5)])
+    d, _ = run_sssp(llp, g, 0)
+    assert d.tolist() == [0, 4, 9]
+
+
+def test_overflow_is_reported(llp):
+    g = csr_from_arcs(3, [(0, 1, 0xF0000000), (1, 2, 0xF0000000)])
+    dg = dev_graph(llp, g)
+    _, ws = llp.sssp(dg, 0)
+    assert llp.get_status(ws)["status"] == llp.LLP_ERR_OVERFLOW
+
+
+def test_deadline_returns_timeout_and_context_survives(llp):
+    """A wait limit that runs out ends the kernel with LLP_ERR_TIMEOUT (no fault);
+    the next call on the same workspace is correct."""
+    n = 20000
+    g = csr_from_arcs(n, [(i, i + 1, 1) for i in range(n - 1)])
+    dg = dev_graph(llp, g)
+    _, ws = llp.sssp(dg, 0, sched=llp.make_sched(deadline_ns=1))
+    assert llp.get_status(ws)["status"] == llp.LLP_ERR_TIMEOUT
+    d, ws = llp.sssp(dg, 0, ws=ws)
+    assert llp.get_status(ws)["status"] == 0
+    assert (llp.as_u32(d) == np.arange(n)).all()
+
+
+@pytest.mark.parametrize("kw", SCHEDS)
+def test_rmat16_schedules(llp, kw):
+    g = synth.rmat(16, seed=21)
+    s = synth.max_out_degree_vertex(g)
+    ref = oracle.sssp(g["offsets"], g["indices"], g["weights"], s)
+    d, _ = run_sssp(llp, g, s, **kw)
+    assert (d == ref).all()
+
+
+@pytest.fixture(scope="module")
+def rmat22():
+    return synth.rmat(22)
+
+
+def test_rmat22_sssp_full(llp, rmat22):
+    """Full-size R-MAT scale 22 (67,108,864 arcs), default schedule as benchmarked."""
+    g = rmat22
+    s = synth.max_out_degree_vertex(g)
+    ref = oracle.sssp(g["offsets"], g["indices"], g["weights"], s)
+    d, st = run_sssp(llp, g, s)
+    assert (d == ref).all()
+
+
+def test_rmat22_bfs_full(llp, rmat22):
+    g = rmat22
+    s = synth.max_out_degree_vertex(g)
+    ref = oracle.bfs(g["offsets"], g["indices"], s)
+    d, _ = run_bfs(llp, g, s)
+    assert (d == ref).all()
+    d64, _ = run_bfs(llp, g, s, offsets_64=True)
+    assert (d64 == ref).all()
