@@ -191,6 +191,7 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = float(np.mean(step_ms))
     st = llp.get_status(ws)
+    slog = llp.sweep_log(ws)
     if world > 1:
         import torch.distributed as dist
         tt = torch.tensor([ms], device=dev)
@@ -261,7 +262,8 @@ def run_gpu(args):
                      "alg_bytes_per_launch": alg_bytes, "kernel": "graph_sweep_kernel<int32,false>"},
         "sweep_stats": {"sweeps": st["sweeps"], "edges_scanned": st["edges"], "advances": st["advances"],
                         "dense_sweeps": st["dense_sweeps"], "edges_per_reached_arc": st["edges"] / max(mr, 1),
-                        "device_loop_ms": st["elapsed_ns"] / 1e6},
+                        "device_loop_ms": st["elapsed_ns"] / 1e6,
+                        "per_sweep": [[round(int(r[0]) / 1e6, 4), int(r[1]), int(r[2]), int(r[3])] for r in slog]},
         "bfs": {"gteps": bfs_mr / (bfs_ms * 1e-3) / 1e9, "ms": bfs_ms, "sweeps": bfs_st["sweeps"],
                 "status": bfs_st["status"]},
         "e2e": {"value": mr / (e2e_ms * 1e-3) / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,

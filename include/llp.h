@@ -114,6 +114,14 @@ const char *llp_status_string(llp_status_t code);
  * that used `ws` into *out.  Returns out->status, or LLP_ERR_CUDA. */
 llp_status_t llp_get_status(const void *ws, void *stream, llp_stats_t *out);
 
+/* Synchronises `stream`, then copies up to max_records per-sweep records of
+ * the last graph-engine call (SSSP/BFS) that used `ws` into out, 4 uint32 per
+ * record: device ns since the call started, small-vertex worklist size, chunk
+ * worklist size, flags (bit 0 dense sweep, bit 1 bucket advance).  Returns the
+ * number of records, or -LLP_ERR_* on error.  Diagnostics and the learned
+ * scheduler's training data; not needed for results. */
+int32_t llp_sweep_log(const void *ws, void *stream, uint32_t *out, int32_t max_records);
+
 /* ------------------------------------------------------------------ SSSP
  * Paper Sec. 4.1: G[v] = d(v); v is forbidden iff some arc (u,v) has
  * d(v) > d(u) + w(u,v); advance sets d(v) to the minimum over such arcs.

@@ -201,3 +201,101 @@ def bfs(g: DeviceGraph, source: int, out=None, sched: Sched | None = None, ws=No
 def as_u32(t: torch.Tensor):
     """View an int32 tensor holding uint32 bit patterns as a numpy uint32 array (host)."""
     return t.cpu().numpy().view("uint32")
+
+
+# ------------------------------------------------------- other LLP problems
+
+def _size(fn, *args):
+    return int(fn(*args))
+
+
+def stable_marriage(men_pref: torch.Tensor, women_rank: torch.Tensor, sched=None, ws=None, stream=None,
+                    want_husband=True, want_next=True):
+    """Man-optimal stable matching.  men_pref/women_rank: int32 [n, n] on the device.
+    Returns (wife, husband|None, next|None, workspace)."""
+    _dev(men_pref, torch.int32, "men_pref"); _dev(women_rank, torch.int32, "women_rank")
+    n = men_pref.shape[0]
+    dev = men_pref.device
+    wife = torch.empty(n, dtype=torch.int32, device=dev)
+    hus = torch.empty(n, dtype=torch.int32, device=dev) if want_husband else None
+    nxt = torch.empty(n, dtype=torch.int32, device=dev) if want_next else None
+    L = lib()
+    if ws is None:
+        ws = workspace(_size(L.llp_stable_marriage_workspace_size, ctypes.c_int32(n)), dev)
+    rc = L.llp_stable_marriage(ctypes.c_int32(n), _ptr(men_pref), _ptr(women_rank), _ptr(wife), _ptr(hus),
+                               _ptr(nxt), None if sched is None else ctypes.byref(sched), _ptr(ws),
+                               ctypes.c_size_t(ws.numel()), _stream(stream))
+    _check(rc, "llp_stable_marriage")
+    return wife, hus, nxt, ws
+
+
+def knapsack(w: torch.Tensor, v: torch.Tensor, capacity: int, want_row=True, sched=None, ws=None, stream=None):
+    """0-1 knapsack optimum.  Returns (best int32[1], final_row int32[capacity+1] | None, workspace)."""
+    _dev(w, torch.int32, "w"); _dev(v, torch.int32, "v")
+    dev = w.device
+    best = torch.empty(1, dtype=torch.int32, device=dev)
+    row = torch.empty(capacity + 1, dtype=torch.int32, device=dev) if want_row else None
+    L = lib()
+    if ws is None:
+        ws = workspace(_size(L.llp_knapsack_workspace_size, ctypes.c_int32(w.shape[0]), ctypes.c_int32(capacity)),
+                       dev)
+    rc = L.llp_knapsack(ctypes.c_int32(w.shape[0]), _ptr(w), _ptr(v), ctypes.c_int32(capacity), _ptr(best),
+                        _ptr(row), None if sched is None else ctypes.byref(sched), _ptr(ws),
+                        ctypes.c_size_t(ws.numel()), _stream(stream))
+    _check(rc, "llp_knapsack")
+    return best, row, ws
+
+
+def transitive_closure(g: DeviceGraph, sched=None, ws=None, stream=None):
+    """Bit-packed reachability: int32 tensor [n, ceil(n/32)] of uint32 bit patterns."""
+    W = (g.n + 31) // 32
+    reach = torch.empty((g.n, W), dtype=torch.int32, device=g.indices.device)
+    L = lib()
+    if ws is None:
+        ws = workspace(_size(L.llp_transitive_closure_workspace_size, ctypes.c_int32(g.n), ctypes.c_int64(g.m)),
+                       g.indices.device)
+    c = g.csr()
+    rc = L.llp_transitive_closure(ctypes.byref(c), _ptr(reach), None if sched is None else ctypes.byref(sched),
+                                  _ptr(ws), ctypes.c_size_t(ws.numel()), _stream(stream))
+    _check(rc, "llp_transitive_closure")
+    return reach, ws
+
+
+def job_schedule(succ: DeviceGraph, duration: torch.Tensor, sched=None, ws=None, stream=None):
+    """Earliest completion times (int32[n]) of a job DAG given by successor arcs."""
+    _dev(duration, torch.int32, "duration")
+    comp = torch.empty(succ.n, dtype=torch.int32, device=duration.device)
+    L = lib()
+    if ws is None:
+        ws = workspace(_size(L.llp_job_schedule_workspace_size, ctypes.c_int32(succ.n), ctypes.c_int64(succ.m)),
+                       duration.device)
+    c = succ.csr()
+    rc = L.llp_job_schedule(ctypes.byref(c), _ptr(duration), _ptr(comp), None if sched is None else ctypes.byref(sched),
+                            _ptr(ws), ctypes.c_size_t(ws.numel()), _stream(stream))
+    _check(rc, "llp_job_schedule")
+    return comp, ws
+
+
+def reduce_sum(x: torch.Tensor, sched=None, ws=None, stream=None):
+    """Sum modulo 2^64 of a uint64 vector (given as int64 bit patterns).  Returns (sum int64[1], ws)."""
+    _dev(x, torch.int64, "x")
+    out = torch.empty(1, dtype=torch.int64, device=x.device)
+    L = lib()
+    if ws is None:
+        ws = workspace(_size(L.llp_reduce_workspace_size, ctypes.c_int64(x.numel())), x.device)
+    rc = L.llp_reduce(ctypes.c_int64(x.numel()), _ptr(x), _ptr(out), None if sched is None else ctypes.byref(sched),
+                      _ptr(ws), ctypes.c_size_t(ws.numel()), _stream(stream))
+    _check(rc, "llp_reduce")
+    return out, ws
+
+
+def sweep_log(ws: torch.Tensor, stream=None, max_records: int = 4096):
+    """Per-sweep records of the last SSSP/BFS call on `ws`: numpy uint32 [k, 4]
+    (device ns since start, small worklist size, chunk worklist size, flags)."""
+    import numpy as np
+    buf = np.zeros((max_records, 4), np.uint32)
+    cnt = lib().llp_sweep_log(_ptr(ws), _stream(stream), buf.ctypes.data_as(ctypes.c_void_p),
+                              ctypes.c_int32(max_records))
+    if cnt < 0:
+        raise LlpError(-cnt, "llp_sweep_log")
+    return buf[:cnt]

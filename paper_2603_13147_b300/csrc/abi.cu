@@ -43,7 +43,7 @@ llp_status_t launch_cooperative(const void *func, int threads, size_t smem, int 
 }
 
 llp_status_t reset_header(void *ws, cudaStream_t stream) {
-    LLP_CUDA_TRY(cudaMemsetAsync(ws, 0, kHeaderBytes, stream));
+    LLP_CUDA_TRY(cudaMemsetAsync(ws, 0, kHeaderZeroBytes, stream));
     return LLP_OK;
 }
 
@@ -84,6 +84,25 @@ llp_status_t llp_get_status(const void *ws, void *stream, llp_stats_t *out) {
     out->block_cfg_used = h.block_cfg_used;
     out->dense_sweeps = h.dense_sweeps;
     return h.status;
+}
+
+int32_t llp_sweep_log(const void *ws, void *stream, uint32_t *out, int32_t max_records) {
+    if (!ws || !out || max_records < 0) return -LLP_ERR_INVALID_ARG;
+    llp::WsHeader h;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
+        cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return -LLP_ERR_CUDA;
+    }
+    int32_t cnt = h.sweeps < 0 ? 0 : h.sweeps;
+    if (cnt > (int32_t)llp::kSweepLogCap) cnt = (int32_t)llp::kSweepLogCap;
+    if (cnt > max_records) cnt = max_records;
+    if (cnt > 0 && cudaMemcpy(out, (const char *)ws + llp::kSweepLogOffset, (size_t)cnt * 16,
+                              cudaMemcpyDeviceToHost) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return -LLP_ERR_CUDA;
+    }
+    return cnt;
 }
 
 }  // extern "C"

@@ -3,28 +3,29 @@
 //
 // State G = dist[] (uint32, 0xFFFFFFFF = "infinity").  A vertex v is forbidden
 // when some arc (u, v) offers d(u) + w(u, v) < d(v); the advance lowers d(v)
-// with atomicMin, which is the lock-free monotone update the paper's
-// requirements list (Sec. 3.2: atomic, monotone, progress detection).  The
-// predicate is evaluated push-style: when u is taken from the worklist, each of
-// its out-arcs is checked, and every successful advance puts v into the next
-// worklist (the paper's problem-specific state selection, Sec. 3.2).
+// with atomicMin, the lock-free monotone update whose requirements the paper
+// lists in Sec. 3.2 (atomic, monotone, progress detection).  The predicate is
+// evaluated push-style: when u is taken from the worklist, each out-arc is
+// checked, and every successful advance makes v a candidate of the next sweep
+// (the paper's problem-specific state selection, Sec. 3.2).
 //
-// One cooperative launch runs all sweeps; sweeps are separated by a bounded
-// grid barrier.  Per sweep k:
-//   - worklist items are (a) "small" vertices (out-degree <= small_max), taken
-//     32 per warp and expanded edge-balanced inside the warp, and (b) chunks of
-//     <= chunk arcs of the larger vertices, one chunk per warp, so hubs are
-//     spread over the whole grid;
-//   - sparse mode walks the small-vertex list; dense mode instead scans every
-//     vertex's stamp (the paper's all-indices solver) and touches the CSR in
-//     vertex order;
-//   - stamp[v] == k marks "v is in the worklist of sweep k"; atomicMax on the
-//     stamp deduplicates appends, appends are warp-aggregated (ballot/popc);
-//   - with a finite bucket width delta (the paper's bucket worklist, Sec. 3.3
-//     "parallel buckets"), only advances with d < current bucket bound enter
-//     the next worklist; the others wait in a far list that is filtered when
-//     the near worklist empties.
-// The sweep stops when no index is forbidden: both worklists are empty.
+// One cooperative launch runs all sweeps, separated by a bounded grid barrier.
+//   - stamp[v] = (sweep << 2) | class, class 0: no out-arcs (never needs a
+//     visit), 1: small (out-degree <= small_max), 2: large.  v belongs to the
+//     worklist of sweep k iff stamp[v] >> 2 == k; atomicMax on the stamp
+//     deduplicates.
+//   - small vertices are taken 32 per warp and their arcs expanded
+//     edge-balanced inside the warp; large vertices are cut into chunks of
+//     chunk_edges arcs, one chunk per warp, so hubs spread over the grid.
+//   - sparse sweeps walk a list of small vertices (built with warp-aggregated
+//     appends); dense sweeps scan every stamp instead (the paper's all-indices
+//     solver) and read the CSR in vertex order.  While a sweep is dense, the
+//     next one is too, and small vertices are then only stamped (no list, no
+//     shared counter in the hot loop; one count per CTA at the end).
+//   - with a finite bucket width delta (the paper's bucket worklist, Sec. 3.3),
+//     only advances with d < current bucket bound enter the next worklist; the
+//     others wait in a far list filtered when the near worklist empties.
+// The run stops when no index is forbidden: both worklists are empty.
 #include <algorithm>
 
 #include "llp_common.cuh"
@@ -39,6 +40,8 @@ struct BlockCfg {
 __host__ __device__ inline BlockCfg block_cfg_of(int c) {
     return c == 1 ? BlockCfg{16, 128} : (c == 3 ? BlockCfg{64, 512} : BlockCfg{32, 256});
 }
+
+constexpr int kUnroll = 4;  // arcs per lane in flight
 
 template <typename OffT>
 struct GraphArgs {
@@ -63,73 +66,101 @@ struct GraphArgs {
     long long deadline_ns;
 };
 
-struct LocalStats {
+struct SweepCtx {
+    uint32_t k;                    // current sweep
+    unsigned long long bucket_hi;  // exclusive bound of the current bucket
+    uint32_t fa;                   // far-list generation
+    bool dense_next;               // small advances are only stamped
     unsigned long long items = 0, edges = 0, adv = 0;
+    uint32_t stamped = 0;          // small vertices stamped for the next sweep (dense_next)
 };
+
+__device__ __forceinline__ uint32_t stamp_word(uint32_t sweep, uint32_t cls) { return (sweep << 2) | cls; }
 
 // Put v (already advanced) into the worklist of sweep k+1.  Warp-collective.
 template <typename OffT>
-__device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, bool want, int32_t v, uint32_t k) {
-    uint32_t deg = 0;
+__device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, bool want, int32_t v, SweepCtx &c) {
+    const uint32_t nk = c.k + 1;
     bool newly = false;
+    uint32_t cls = 0;
     if (want) {
-        const OffT b = __ldg(a.off + v);
-        const OffT e = __ldg(a.off + v + 1);
-        deg = (uint32_t)(e - b);
-        if (deg > 0) newly = atomicMax(a.stamp + v, k + 1) < k + 1;
+        const uint32_t s = __ldcg(a.stamp + v);
+        cls = s & 3u;
+        if (cls != 0 && (s >> 2) < nk) {
+            if (c.dense_next && cls == 1) {
+                atomicMax(a.stamp + v, stamp_word(nk, 1));  // result unused: a reduction
+                c.stamped++;
+            } else {
+                newly = (atomicMax(a.stamp + v, stamp_word(nk, cls)) >> 2) < nk;
+            }
+        }
     }
-    const uint32_t nx = (k + 1) % 3;
-    const bool is_small = newly && deg <= (uint32_t)a.small_max;
-    const bool is_large = newly && deg > (uint32_t)a.small_max;
-    const uint32_t slot = warp_append_slot(is_small, &a.h->n_small[nx]);
-    if (is_small) a.small[(k + 1) & 1][slot] = v;
-    const uint32_t nch = is_large ? (deg + a.chunk_edges - 1) / a.chunk_edges : 0u;
-    const uint32_t base = warp_reserve(nch, &a.h->n_chunk[nx]);
-    int2 *dst = a.chunk[(k + 1) & 1] + base;
-    for (uint32_t c = 0; c < nch; c++) dst[c] = make_int2(v, (int)c);
+    const uint32_t nx = nk % 3;
+    const bool is_small = newly && cls == 1;
+    const bool is_large = newly && cls == 2;
+    if (__any_sync(0xffffffffu, is_small)) {
+        const uint32_t slot = warp_append_slot(is_small, &a.h->n_small[nx]);
+        if (is_small) a.small[nk & 1][slot] = v;
+    }
+    if (__any_sync(0xffffffffu, is_large)) {
+        uint32_t nch = 0;
+        if (is_large) {
+            const uint32_t deg = (uint32_t)(__ldg(a.off + v + 1) - __ldg(a.off + v));
+            nch = (deg + a.chunk_edges - 1) / a.chunk_edges;
+        }
+        const uint32_t base = warp_reserve(nch, &a.h->n_chunk[nx]);
+        int2 *dst = a.chunk[nk & 1] + base;
+        for (uint32_t q = 0; q < nch; q++) dst[q] = make_int2(v, (int)q);
+    }
 }
 
-// Evaluate forbidden(v) against one candidate and advance.  Warp-collective:
-// all 32 lanes call it; `valid` masks lanes without an arc.
+// Evaluate forbidden(v) against candidate distances and advance, for up to
+// kUnroll arcs per lane.  Warp-collective.
 template <typename OffT>
-__device__ __forceinline__ void relax(const GraphArgs<OffT> &a, bool valid, int32_t v, uint64_t cand64, uint32_t k,
-                                      unsigned long long bucket_hi, uint32_t fa, LocalStats &st) {
-    bool improved = false;
-    uint32_t cand = 0;
-    if (valid) {
-        if (cand64 >= (uint64_t)kInf) {
-            set_status(a.h, LLP_ERR_OVERFLOW);
-        } else {
-            cand = (uint32_t)cand64;
-            const uint32_t dv = __ldcg(a.dist + v);
-            if (cand < dv) {
-                const uint32_t old = atomicMin(a.dist + v, cand);
-                improved = cand < old;
+__device__ __forceinline__ void relax_multi(const GraphArgs<OffT> &a, const bool (&ok)[kUnroll],
+                                            const int32_t (&v)[kUnroll], const uint64_t (&cand64)[kUnroll],
+                                            SweepCtx &c) {
+    uint32_t dv[kUnroll];
+#pragma unroll
+    for (int j = 0; j < kUnroll; j++) dv[j] = ok[j] ? __ldcg(a.dist + v[j]) : 0u;
+    bool improved[kUnroll];
+#pragma unroll
+    for (int j = 0; j < kUnroll; j++) {
+        improved[j] = false;
+        if (ok[j]) {
+            if (cand64[j] >= (uint64_t)kInf) {
+                set_status(a.h, LLP_ERR_OVERFLOW);
+            } else if ((uint32_t)cand64[j] < dv[j]) {
+                improved[j] = (uint32_t)cand64[j] < atomicMin(a.dist + v[j], (uint32_t)cand64[j]);
             }
         }
+        c.adv += improved[j];
     }
-    st.adv += improved;
-    bool near = improved && (unsigned long long)cand < bucket_hi;
-    const bool far = improved && !near;
-    if (__any_sync(0xffffffffu, far)) {
-        const uint32_t slot = warp_append_slot(far, &a.h->n_far[fa % 3]);
-        if (far) {
-            if (slot < a.far_cap) {
-                a.far[fa & 1][slot] = make_int2(v, (int)cand);
-                atomicMin(&a.h->far_min[fa % 3], cand);
-            } else {
-                near = true;  // far list full: keep it in the near worklist (still correct)
+#pragma unroll
+    for (int j = 0; j < kUnroll; j++) {
+        if (!__any_sync(0xffffffffu, improved[j])) continue;
+        const uint32_t cand = (uint32_t)cand64[j];
+        bool near = improved[j] && (unsigned long long)cand < c.bucket_hi;
+        const bool far = improved[j] && !near;
+        if (__any_sync(0xffffffffu, far)) {
+            const uint32_t slot = warp_append_slot(far, &a.h->n_far[c.fa % 3]);
+            if (far) {
+                if (slot < a.far_cap) {
+                    a.far[c.fa & 1][slot] = make_int2(v[j], (int)cand);
+                    atomicMin(&a.h->far_min[c.fa % 3], cand);
+                } else {
+                    near = true;  // far list full: keep it in the near worklist (still correct)
+                }
             }
         }
+        push_near(a, near, v[j], c);
     }
-    if (__any_sync(0xffffffffu, near)) push_near(a, near, v, k);
 }
 
 // Expand the out-arcs of up to 32 small vertices (one per lane) edge-balanced
-// across the warp.
+// across the warp, kUnroll batches of 32 arcs at a time.
 template <typename OffT, bool UNIT>
-__device__ __forceinline__ void expand_group(const GraphArgs<OffT> &a, bool valid, int32_t u, uint32_t k,
-                                             unsigned long long bucket_hi, uint32_t fa, LocalStats &st) {
+__device__ __forceinline__ void expand_group(const GraphArgs<OffT> &a, bool valid, int32_t u, SweepCtx &c) {
     uint32_t du = 0, deg = 0;
     OffT beg = 0;
     if (valid) {
@@ -137,7 +168,7 @@ __device__ __forceinline__ void expand_group(const GraphArgs<OffT> &a, bool vali
         beg = __ldg(a.off + u);
         deg = (uint32_t)(__ldg(a.off + u + 1) - beg);
     }
-    st.items += valid;
+    c.items += valid;
     uint32_t incl = deg;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -146,35 +177,41 @@ __device__ __forceinline__ void expand_group(const GraphArgs<OffT> &a, bool vali
     }
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     const uint32_t excl = incl - deg;
-    st.edges += (lane_id() == 0) ? total : 0;
-    for (uint32_t base = 0; base < total; base += 32) {
-        const uint32_t t = base + lane_id();
-        int pos = 0;
+    c.edges += (lane_id() == 0) ? total : 0;
+    for (uint32_t base = 0; base < total; base += 32 * kUnroll) {
+        bool ok[kUnroll];
+        int32_t v[kUnroll];
+        uint64_t cand[kUnroll];
 #pragma unroll
-        for (int s = 16; s > 0; s >>= 1) {
-            const uint32_t probe = __shfl_sync(0xffffffffu, incl, pos + s - 1);
-            if (probe <= t) pos += s;
+        for (int j = 0; j < kUnroll; j++) {
+            const uint32_t t = base + 32 * j + lane_id();
+            int pos = 0;
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                const uint32_t probe = __shfl_sync(0xffffffffu, incl, pos + s - 1);
+                if (probe <= t) pos += s;
+            }
+            ok[j] = t < total;
+            const int owner = ok[j] ? pos : 0;
+            const uint32_t ex = __shfl_sync(0xffffffffu, excl, owner);
+            const OffT bo = __shfl_sync(0xffffffffu, beg, owner);
+            const uint32_t dq = __shfl_sync(0xffffffffu, du, owner);
+            v[j] = 0;
+            uint32_t w = 0;
+            if (ok[j]) {
+                const OffT e = bo + (OffT)(t - ex);
+                v[j] = __ldg(a.idx + e);
+                w = UNIT ? 1u : __ldg(a.w + e);
+            }
+            cand[j] = (uint64_t)dq + w;
         }
-        const bool ok = t < total;
-        const int owner = ok ? pos : 0;
-        const uint32_t ex = __shfl_sync(0xffffffffu, excl, owner);
-        const OffT bo = __shfl_sync(0xffffffffu, beg, owner);
-        const uint32_t dq = __shfl_sync(0xffffffffu, du, owner);
-        int32_t v = 0;
-        uint32_t w = 0;
-        if (ok) {
-            const OffT e = bo + (OffT)(t - ex);
-            v = __ldg(a.idx + e);
-            w = UNIT ? 1u : __ldg(a.w + e);
-        }
-        relax(a, ok, v, (uint64_t)dq + w, k, bucket_hi, fa, st);
+        relax_multi(a, ok, v, cand, c);
     }
 }
 
 // One chunk (<= chunk_edges arcs) of one large vertex.
 template <typename OffT, bool UNIT>
-__device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item, uint32_t k,
-                                             unsigned long long bucket_hi, uint32_t fa, LocalStats &st) {
+__device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item, SweepCtx &c) {
     const int32_t u = item.x;
     uint32_t su = 0, du = 0;
     if (lane_id() == 0) {
@@ -183,44 +220,66 @@ __device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item
     }
     su = __shfl_sync(0xffffffffu, su, 0);
     du = __shfl_sync(0xffffffffu, du, 0);
-    if (su != k) return;  // re-advanced meanwhile: sweep k+1 handles it (warp-uniform)
+    if ((su >> 2) != c.k) return;  // re-advanced meanwhile: sweep k+1 handles it (warp-uniform)
     const OffT b0 = __ldg(a.off + u);
     const OffT e0 = __ldg(a.off + u + 1);
     const OffT beg = b0 + (OffT)item.y * (OffT)a.chunk_edges;
     const OffT end = min(e0, beg + (OffT)a.chunk_edges);
-    st.items += (lane_id() == 0 && item.y == 0);
-    st.edges += (lane_id() == 0) ? (unsigned long long)(end - beg) : 0ull;
-    for (OffT base = beg; base < end; base += 32) {
-        const OffT e = base + lane_id();
-        const bool ok = e < end;
-        int32_t v = 0;
-        uint32_t w = 0;
-        if (ok) {
-            v = __ldg(a.idx + e);
-            w = UNIT ? 1u : __ldg(a.w + e);
+    c.items += (lane_id() == 0 && item.y == 0);
+    c.edges += (lane_id() == 0) ? (unsigned long long)(end - beg) : 0ull;
+    for (OffT base = beg; base < end; base += 32 * kUnroll) {
+        bool ok[kUnroll];
+        int32_t v[kUnroll];
+        uint64_t cand[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) {
+            const OffT e = base + 32 * j + lane_id();
+            ok[j] = e < end;
+            v[j] = 0;
+            uint32_t w = 0;
+            if (ok[j]) {
+                v[j] = __ldg(a.idx + e);
+                w = UNIT ? 1u : __ldg(a.w + e);
+            }
+            cand[j] = (uint64_t)du + w;
         }
-        relax(a, ok, v, (uint64_t)du + w, k, bucket_hi, fa, st);
+        relax_multi(a, ok, v, cand, c);
+    }
+}
+
+// Adds the CTA's dense_next stamp count to the next sweep's counter.
+__device__ __forceinline__ void flush_stamped(WsHeader *h, SweepCtx &c, uint32_t *s_cnt) {
+    const uint32_t ws = warp_sum(c.stamped);
+    c.stamped = 0;
+    if (lane_id() == 0 && ws) atomicAdd(s_cnt, ws);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t t = *s_cnt;
+        *s_cnt = 0;
+        if (t) atomicAdd(&h->n_small[(c.k + 1) % 3], t);
     }
 }
 
 template <typename OffT, bool UNIT>
-__global__ void __launch_bounds__(512) graph_sweep_kernel(GraphArgs<OffT> a) {
+__global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) {
+    __shared__ uint32_t s_cnt;
     WsHeader *h = a.h;
     const long long t0 = globaltimer_ns();
     const long long deadline = t0 + a.deadline_ns;
     uint32_t phase = 0;
-    LocalStats st;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
     const int warps_per_block = blockDim.x >> 5;
     const int64_t gwarp = (int64_t)blockIdx.x * warps_per_block + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
+    if (threadIdx.x == 0) s_cnt = 0;
 
     // ---- init_global_state / initial_states_to_process (paper Sec. 3.3)
-    const uint32_t src_deg = (uint32_t)(__ldg(a.off + a.source + 1) - __ldg(a.off + a.source));
     for (int64_t v = gtid; v < a.n; v += gthreads) {
+        const uint32_t deg = (uint32_t)(__ldg(a.off + v + 1) - __ldg(a.off + v));
+        const uint32_t cls = deg == 0 ? 0u : (deg <= (uint32_t)a.small_max ? 1u : 2u);
         a.dist[v] = (v == a.source) ? 0u : kInf;
-        a.stamp[v] = (v == a.source && src_deg > 0) ? 1u : 0u;
+        a.stamp[v] = stamp_word((v == a.source && cls) ? 1u : 0u, cls);
     }
     if (gtid == 0) {
         h->t_start = t0;
@@ -228,44 +287,61 @@ __global__ void __launch_bounds__(512) graph_sweep_kernel(GraphArgs<OffT> a) {
         h->delta_used = a.delta;
         h->block_cfg_used = a.cfg;
         for (int i = 0; i < 3; i++) h->far_min[i] = kInf;
+        h->list_ok[1] = 1;
+        const uint32_t src_deg = (uint32_t)(__ldg(a.off + a.source + 1) - __ldg(a.off + a.source));
         if (src_deg > 0) {
             if (src_deg <= (uint32_t)a.small_max) {
                 a.small[1][0] = a.source;
                 h->n_small[1] = 1;
             } else {
                 const uint32_t nch = (src_deg + a.chunk_edges - 1) / a.chunk_edges;
-                for (uint32_t c = 0; c < nch; c++) a.chunk[1][c] = make_int2(a.source, (int)c);
+                for (uint32_t q = 0; q < nch; q++) a.chunk[1][q] = make_int2(a.source, (int)q);
                 h->n_chunk[1] = nch;
             }
         }
     }
     bool alive = grid_barrier(h, phase, deadline);
 
-    uint32_t k = 1, fa = 0, dense_sweeps = 0;
-    unsigned long long bucket_hi = (a.delta == kInf) ? (1ull << 40) : (unsigned long long)a.delta;
+    SweepCtx c;
+    c.k = 1;
+    c.fa = 0;
+    c.bucket_hi = (a.delta == kInf) ? (1ull << 40) : (unsigned long long)a.delta;
+    uint32_t dense_sweeps = 0;
     while (alive) {
+        const uint32_t k = c.k;
         const uint32_t ns = *(volatile uint32_t *)&h->n_small[k % 3];
         const uint32_t nc = *(volatile uint32_t *)&h->n_chunk[k % 3];
+        const bool list_ok = *(volatile uint32_t *)&h->list_ok[k % 3] != 0;
+        const bool dense = ns + nc > 0 &&
+                           (!list_ok || a.mode == LLP_MODE_DENSE || (a.mode == LLP_MODE_AUTO && ns > a.dense_thresh));
+        c.dense_next = dense && a.mode != LLP_MODE_SPARSE;
         if (gtid == 0) {
             const uint32_t r = (k + 2) % 3;
             h->n_small[r] = 0;
             h->n_chunk[r] = 0;
+            h->list_ok[r] = 0;
+            h->list_ok[(k + 1) % 3] = c.dense_next ? 0u : 1u;
+            if (k - 1 < kSweepLogCap)
+                sweep_log(h)[k - 1] = SweepRec{(uint32_t)(globaltimer_ns() - t0), ns, nc,
+                                               (dense ? 1u : 0u) | (ns + nc == 0 ? 2u : 0u)};
         }
         if (ns + nc == 0) {
             // near worklist empty: move to the next non-empty bucket, or stop
-            const uint32_t nf_raw = *(volatile uint32_t *)&h->n_far[fa % 3];
+            const uint32_t nf_raw = *(volatile uint32_t *)&h->n_far[c.fa % 3];
             const uint32_t nf = min(nf_raw, a.far_cap);
             if (nf == 0) break;
-            const unsigned long long fmin = *(volatile uint32_t *)&h->far_min[fa % 3];
+            c.dense_next = false;
+            const unsigned long long fmin = *(volatile uint32_t *)&h->far_min[c.fa % 3];
             const unsigned long long dl = a.delta;
             unsigned long long nh = (fmin / dl + 1ull) * dl;
-            if (nh < bucket_hi + dl) nh = bucket_hi + dl;
+            if (nh < c.bucket_hi + dl) nh = c.bucket_hi + dl;
             if (gtid == 0) {
-                h->n_far[(fa + 2) % 3] = 0;
-                h->far_min[(fa + 2) % 3] = kInf;
+                h->n_far[(c.fa + 2) % 3] = 0;
+                h->far_min[(c.fa + 2) % 3] = kInf;
+                h->list_ok[(k + 1) % 3] = 1;
                 h->aux += 1;
             }
-            const int2 *fl = a.far[fa & 1];
+            const int2 *fl = a.far[c.fa & 1];
             for (int64_t base = gwarp * 32; base < nf; base += nwarps * 32) {
                 const int64_t i = base + lane_id();
                 const bool ok = i < nf;
@@ -277,29 +353,29 @@ __global__ void __launch_bounds__(512) graph_sweep_kernel(GraphArgs<OffT> a) {
                 }
                 bool to_near = live && (unsigned long long)(uint32_t)e.y < nh;
                 const bool keep = live && !to_near;
-                const uint32_t slot = warp_append_slot(keep, &h->n_far[(fa + 1) % 3]);
+                const uint32_t slot = warp_append_slot(keep, &h->n_far[(c.fa + 1) % 3]);
                 if (keep) {
                     if (slot < a.far_cap) {
-                        a.far[(fa + 1) & 1][slot] = e;
-                        atomicMin(&h->far_min[(fa + 1) % 3], (uint32_t)e.y);
+                        a.far[(c.fa + 1) & 1][slot] = e;
+                        atomicMin(&h->far_min[(c.fa + 1) % 3], (uint32_t)e.y);
                     } else {
                         to_near = true;
                     }
                 }
-                push_near(a, to_near, e.x, k);
+                push_near(a, to_near, e.x, c);
             }
-            bucket_hi = nh;
-            fa += 1;
+            c.bucket_hi = nh;
+            c.fa += 1;
         } else {
-            const bool dense = a.mode == LLP_MODE_DENSE || (a.mode == LLP_MODE_AUTO && ns > a.dense_thresh);
             dense_sweeps += dense;
-            const uint32_t ngroups = dense ? (uint32_t)(((int64_t)a.n + 31) / 32) : (uint32_t)(((uint64_t)ns + 31) / 32);
+            const uint32_t ngroups =
+                dense ? (uint32_t)(((int64_t)a.n + 31) / 32) : (uint32_t)(((uint64_t)ns + 31) / 32);
             const int2 *cl = a.chunk[k & 1];
             const int32_t *sl = a.small[k & 1];
             const int64_t total = (int64_t)nc + ngroups;
             for (int64_t it = gwarp; it < total; it += nwarps) {
                 if (it < nc) {
-                    expand_chunk<OffT, UNIT>(a, cl[it], k, bucket_hi, fa, st);
+                    expand_chunk<OffT, UNIT>(a, cl[it], c);
                 } else {
                     const int64_t g = it - nc;
                     int32_t u = 0;
@@ -308,31 +384,31 @@ __global__ void __launch_bounds__(512) graph_sweep_kernel(GraphArgs<OffT> a) {
                         const int64_t vv = g * 32 + lane_id();
                         ok = vv < a.n;
                         u = ok ? (int32_t)vv : 0;
-                        if (ok) ok = __ldcg(a.stamp + u) == k;
-                        if (ok) ok = (__ldg(a.off + u + 1) - __ldg(a.off + u)) <= (OffT)a.small_max;
+                        if (ok) ok = __ldcg(a.stamp + u) == stamp_word(k, 1);
                     } else {
                         const int64_t i = g * 32 + lane_id();
                         ok = i < ns;
                         u = ok ? sl[i] : 0;
-                        if (ok) ok = __ldcg(a.stamp + u) == k;
+                        if (ok) ok = (__ldcg(a.stamp + u) >> 2) == k;
                     }
-                    expand_group<OffT, UNIT>(a, ok, u, k, bucket_hi, fa, st);
+                    expand_group<OffT, UNIT>(a, ok, u, c);
                 }
             }
         }
+        flush_stamped(h, c, &s_cnt);
         alive = grid_barrier(h, phase, deadline);
-        k += 1;
+        c.k += 1;
     }
 
     // ---- statistics (one atomic per warp)
-    const unsigned long long it_s = warp_sum(st.items), ed_s = warp_sum(st.edges), ad_s = warp_sum(st.adv);
+    const unsigned long long it_s = warp_sum(c.items), ed_s = warp_sum(c.edges), ad_s = warp_sum(c.adv);
     if (lane_id() == 0) {
         atomicAdd(&h->items, it_s);
         atomicAdd(&h->edges, ed_s);
         atomicAdd(&h->advances, ad_s);
     }
     if (gtid == 0) {
-        h->sweeps = (int32_t)k;
+        h->sweeps = (int32_t)c.k;
         h->dense_sweeps = (int32_t)dense_sweeps;
     }
     __syncthreads();
@@ -355,6 +431,7 @@ struct Layout {
 Layout carve_graph(void *ws, int32_t n, int64_t m) {
     Carve c(ws);
     Layout L;
+    // chunks of one sweep: sum over large v of ceil(deg/chunk) <= m/128 + m/17
     const size_t chunk_cap = (size_t)(m / 128 + m / 16 + 2);
     L.far_cap = (uint32_t)std::max<int64_t>(n, 1024);
     L.stamp = c.take<uint32_t>(n);
@@ -388,7 +465,7 @@ template <bool UNIT>
 llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, const llp_sched_t *s, void *ws,
                          size_t ws_bytes, cudaStream_t stream) {
     if (!g || !out || !ws) return LLP_ERR_INVALID_ARG;
-    if (g->n < 1 || g->m < 0 || !g->offsets) return LLP_ERR_INVALID_ARG;
+    if (g->n < 1 || g->n > (1 << 29) || g->m < 0 || !g->offsets) return LLP_ERR_INVALID_ARG;
     if (g->m > 0 && (!g->indices || (!UNIT && !g->weights))) return LLP_ERR_INVALID_ARG;
     if (!g->offsets_64 && g->m > 0x7FFFFFFFll) return LLP_ERR_INVALID_ARG;
     if (source < 0 || source >= g->n) return LLP_ERR_INVALID_ARG;
@@ -403,6 +480,7 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
     const BlockCfg bc = block_cfg_of(cfg);
     llp_status_t rc = reset_header(ws, stream);
     if (rc != LLP_OK) return rc;
+
     auto fill = [&](auto &args) {
         args.n = g->n;
         args.source = source;

@@ -10,7 +10,22 @@
 namespace llp {
 
 constexpr int64_t kDefaultDeadlineNs = 10LL * 1000 * 1000 * 1000;  // 10 s
-constexpr size_t kHeaderBytes = 4096;
+constexpr size_t kHeaderBytes = 65536;  // WsHeader, then the sweep log
+constexpr size_t kHeaderZeroBytes = 4096;  // part of the header cleared per call
+constexpr size_t kSweepLogOffset = 4096;
+constexpr uint32_t kSweepLogCap = (uint32_t)((kHeaderBytes - kSweepLogOffset) / 16);
+
+// One record per sweep (graph engine): device time since the call started,
+// worklist sizes at the start of the sweep and flags (bit 0 dense sweep,
+// bit 1 bucket advance).
+struct SweepRec {
+    uint32_t t_ns;
+    uint32_t n_small;
+    uint32_t n_chunk;
+    uint32_t flags;
+};
+
+__device__ __forceinline__ SweepRec *sweep_log(void *h) { return (SweepRec *)((char *)h + kSweepLogOffset); }
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 
 // Workspace header: the first kHeaderBytes of every workspace.  Zeroed by the
@@ -39,9 +54,10 @@ struct alignas(256) WsHeader {
     alignas(128) uint32_t work[3];
     alignas(128) uint32_t n_far[3];
     uint32_t far_min[3];
+    uint32_t list_ok[3];
     uint32_t scratch[16];
 };
-static_assert(sizeof(WsHeader) <= kHeaderBytes, "header too large");
+static_assert(sizeof(WsHeader) <= kHeaderZeroBytes, "header too large");
 
 // ------------------------------------------------------------ device helpers
 

@@ -66,9 +66,10 @@ __device__ __forceinline__ unsigned long long propose_chain(int32_t m, int32_t k
 // down in chunks of blockDim.x * R cells: every cell of a chunk computes
 // max(G[k-1,c], v_k + G[k-1,c-w_k]) into registers, the CTA synchronises, then
 // writes; cells below the chunk are still G[k-1, *] when read, so one buffer
-// suffices.  Returns false on overflow (sum of values >= 2^31).
+// suffices.  Items with w < 1 or v < 0 set LLP_ERR_INVALID_ARG in h.
 template <int R>
-__device__ __forceinline__ void knapsack_cta(int32_t n, const int32_t *w, const int32_t *v, int32_t W, int32_t *row) {
+__device__ __forceinline__ void knapsack_cta(int32_t n, const int32_t *w, const int32_t *v, int32_t W, int32_t *row,
+                                             WsHeader *h) {
     const int T = blockDim.x;
     for (int32_t c = threadIdx.x; c <= W; c += T) row[c] = 0;
     __syncthreads();
@@ -77,6 +78,10 @@ __device__ __forceinline__ void knapsack_cta(int32_t n, const int32_t *w, const 
         const int32_t wk = __ldg(w + k);
         const int32_t vk = __ldg(v + k);
         if (wk > W) continue;  // item never fits: row unchanged (uniform branch)
+        if (wk < 1 || vk < 0) {  // outside the problem statement: report, skip
+            if (threadIdx.x == 0 && h) set_status(h, LLP_ERR_INVALID_ARG);
+            continue;
+        }
         // chunks from the top; the lowest chunk may be partial
         for (int64_t top = (int64_t)W + 1; top > wk; top -= chunk) {
             const int64_t lo = top - chunk > wk ? top - chunk : (int64_t)wk;
