@@ -1,31 +1,39 @@
 // Persistent forbidden/advance sweep engine for the graph problems:
 // SSSP (paper Sec. 4.1) and BFS (paper Sec. 4.2).
 //
-// State G = dist[] (uint32, 0xFFFFFFFF = "infinity").  A vertex v is forbidden
+// State G[v] = d(v) (uint32, 0xFFFFFFFF = "infinity"), kept during the run in
+// the high half of a 64-bit word key[v] = d(v) << 32 | class(v) so that the one
+// load that evaluates the predicate also yields how v is scheduled; the result
+// is copied to dist[] when the run ends.  A vertex v is forbidden
 // when some arc (u, v) offers d(u) + w(u, v) < d(v); the advance lowers d(v)
-// with atomicMin, the lock-free monotone update whose requirements the paper
-// lists in Sec. 3.2 (atomic, monotone, progress detection).  The predicate is
-// evaluated push-style: when u is taken from the worklist, each out-arc is
-// checked, and every successful advance makes v a candidate of the next sweep
+// with an atomic min, the lock-free monotone update whose requirements the
+// paper lists in Sec. 3.2 (atomic, monotone, progress detection).  The
+// predicate is evaluated push-style: when u is taken from the worklist each
+// out-arc is checked, and every advance makes v a candidate of the next sweep
 // (the paper's problem-specific state selection, Sec. 3.2).
 //
 // One cooperative launch runs all sweeps, separated by a bounded grid barrier.
-//   - stamp[v] = (sweep << 2) | class, class 0: no out-arcs (never needs a
-//     visit), 1: small (out-degree <= small_max), 2: large.  v belongs to the
-//     worklist of sweep k iff stamp[v] >> 2 == k; atomicMax on the stamp
-//     deduplicates.
-//   - small vertices are taken 32 per warp and their arcs expanded
-//     edge-balanced inside the warp; large vertices are cut into chunks of
-//     chunk_edges arcs, one chunk per warp, so hubs spread over the grid.
-//   - sparse sweeps walk a list of small vertices (built with warp-aggregated
-//     appends); dense sweeps scan every stamp instead (the paper's all-indices
-//     solver) and read the CSR in vertex order.  While a sweep is dense, the
-//     next one is too, and small vertices are then only stamped (no list, no
-//     shared counter in the hot loop; one count per CTA at the end).
-//   - with a finite bucket width delta (the paper's bucket worklist, Sec. 3.3),
-//     only advances with d < current bucket bound enter the next worklist; the
-//     others wait in a far list filtered when the near worklist empties.
-// The run stops when no index is forbidden: both worklists are empty.
+//   - the worklist of sweep k is a bitmap B_k (one bit per vertex, two buffers
+//     by parity); atomicOr on B_{k+1} deduplicates advances, and the consumer
+//     of sweep k clears B_k as it reads it, so B_k is clean when it becomes
+//     B_{k+2};
+//   - a per-vertex class (1: small, out-degree <= small_max; 2: large; 0: no
+//     out-arcs), computed once per call into key[] and a per-32-vertex table, routes
+//     advanced vertices: large ones go to a chunk list (chunks of chunk_edges
+//     arcs, one per warp, so hubs spread over the grid), small ones either to a
+//     list (sparse sweep, warp-aggregated appends) or only to the bitmap (dense
+//     sweep: fire-and-forget atomicOr, the next sweep scans the bitmap like the
+//     paper's all-indices solver, without any shared counter in the hot loop);
+//   - small vertices are expanded 32 per warp, arcs balanced across the lanes;
+//   - the advance itself is a fire-and-forget 64-bit atomic min on key[v]
+//     issued when the candidate beats the value just read (a stale read only
+//     costs a redundant visit: distances only decrease; the class bits are the
+//     same on both sides of the min);
+//   - with a finite bucket width delta (the paper's bucket worklist, Sec. 3.3)
+//     only advances with d below the current bucket bound enter the next
+//     worklist; the others wait in a far list filtered when the near worklist
+//     empties.
+// The run stops when no index is forbidden: every worklist is empty.
 #include <algorithm>
 
 #include "llp_common.cuh"
@@ -42,16 +50,23 @@ __host__ __device__ inline BlockCfg block_cfg_of(int c) {
 }
 
 constexpr int kUnroll = 4;  // arcs per lane in flight
+#ifndef LLP_DENSE_GROUP_WORDS
+#define LLP_DENSE_GROUP_WORDS 8
+#endif
+constexpr int kGroupWords = LLP_DENSE_GROUP_WORDS;  // bitmap words per dense-sweep item
 
 template <typename OffT>
 struct GraphArgs {
     int32_t n;
     int32_t source;
+    int32_t nwords;  // ceil(n / 32)
     const OffT *off;
     const int32_t *idx;
     const uint32_t *w;
-    uint32_t *dist;
-    uint32_t *stamp;
+    uint32_t *dist;                 // output
+    unsigned long long *key;        // d << 32 | class during the run
+    uint2 *cls;      // per 32 vertices: x = has out-arcs, y = large
+    uint32_t *bm[2]; // frontier bitmaps by sweep parity
     int32_t *small[2];
     int2 *chunk[2];
     int2 *far[2];
@@ -59,7 +74,7 @@ struct GraphArgs {
     WsHeader *h;
     uint32_t delta;  // kInf: no buckets
     int32_t mode;
-    uint32_t dense_thresh;
+    unsigned long long dense_arcs;  // AUTO: dense next sweep when this sweep's arcs exceed it
     int32_t small_max;
     int32_t chunk_edges;
     int32_t cfg;
@@ -70,47 +85,124 @@ struct SweepCtx {
     uint32_t k;                    // current sweep
     unsigned long long bucket_hi;  // exclusive bound of the current bucket
     uint32_t fa;                   // far-list generation
-    bool dense_next;               // small advances are only stamped
+    bool dense_next;               // small advances only set their bitmap bit
+    uint32_t *bm_cur, *bm_next;
     unsigned long long items = 0, edges = 0, adv = 0;
-    uint32_t stamped = 0;          // small vertices stamped for the next sweep (dense_next)
+    uint32_t marked = 0;           // dense_next marks (an upper bound of the next frontier)
+    // per-warp shared-memory staging of worklist appends (warp-uniform counts)
+    int32_t *st_small;
+    int2 *st_chunk;
+    uint32_t st_ns = 0, st_nc = 0;
 };
 
-__device__ __forceinline__ uint32_t stamp_word(uint32_t sweep, uint32_t cls) { return (sweep << 2) | cls; }
+constexpr uint32_t kStageSmall = 128;  // entries per warp
+constexpr uint32_t kStageChunk = 256;
+constexpr uint32_t kDirectChunks = 8;  // a lane with more chunk entries reserves them directly
 
-// Put v (already advanced) into the worklist of sweep k+1.  Warp-collective.
-template <typename OffT>
-__device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, bool want, int32_t v, SweepCtx &c) {
-    const uint32_t nk = c.k + 1;
-    bool newly = false;
-    uint32_t cls = 0;
-    if (want) {
-        const uint32_t s = __ldcg(a.stamp + v);
-        cls = s & 3u;
-        if (cls != 0 && (s >> 2) < nk) {
-            if (c.dense_next && cls == 1) {
-                atomicMax(a.stamp + v, stamp_word(nk, 1));  // result unused: a reduction
-                c.stamped++;
+// Moves a warp's staged entries to the global list (one reservation).
+template <typename T>
+__device__ __forceinline__ void stage_flush(T *stage, uint32_t &cnt, T *list, uint32_t *counter) {
+    if (cnt == 0) return;
+    __syncwarp();
+    uint32_t base = 0;
+    if (lane_id() == 0) base = atomicAdd(counter, cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (uint32_t i = lane_id(); i < cnt; i += 32) list[base + i] = stage[i];
+    __syncwarp();
+    cnt = 0;
+}
+
+__device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_and(uint32_t *p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.and.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_min64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t key_dist(unsigned long long kv) { return (uint32_t)(kv >> 32); }
+
+// Put the advanced vertices v[j] (want[j], class cls[j]) into the worklist of
+// sweep k+1, all kUnroll of them at once.  Warp-collective.
+template <typename OffT, int U>
+__device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, const bool (&want)[U], const int32_t (&v)[U],
+                                          const uint32_t (&cls)[U], SweepCtx &c) {
+    bool newly[U];
+    uint32_t n_small = 0, n_large = 0;
+#pragma unroll
+    for (int j = 0; j < U; j++) {
+        newly[j] = false;
+        if (want[j] && cls[j] != 0) {
+            const uint32_t bit = 1u << (v[j] & 31);
+            uint32_t *word = c.bm_next + (v[j] >> 5);
+            if (c.dense_next && cls[j] == 1) {
+                red_or(word, bit);
+                c.marked++;
             } else {
-                newly = (atomicMax(a.stamp + v, stamp_word(nk, cls)) >> 2) < nk;
+                newly[j] = (atomicOr(word, bit) & bit) == 0;
             }
         }
     }
-    const uint32_t nx = nk % 3;
-    const bool is_small = newly && cls == 1;
-    const bool is_large = newly && cls == 2;
-    if (__any_sync(0xffffffffu, is_small)) {
-        const uint32_t slot = warp_append_slot(is_small, &a.h->n_small[nx]);
-        if (is_small) a.small[nk & 1][slot] = v;
-    }
-    if (__any_sync(0xffffffffu, is_large)) {
-        uint32_t nch = 0;
-        if (is_large) {
-            const uint32_t deg = (uint32_t)(__ldg(a.off + v + 1) - __ldg(a.off + v));
-            nch = (deg + a.chunk_edges - 1) / a.chunk_edges;
+    uint32_t nch[U];
+#pragma unroll
+    for (int j = 0; j < U; j++) {
+        nch[j] = 0;
+        n_small += (newly[j] && cls[j] == 1);
+        if (newly[j] && cls[j] == 2) {
+            const uint32_t deg = (uint32_t)(__ldg(a.off + v[j] + 1) - __ldg(a.off + v[j]));
+            nch[j] = (deg + a.chunk_edges - 1) / a.chunk_edges;
+            n_large += nch[j];
         }
-        const uint32_t base = warp_reserve(nch, &a.h->n_chunk[nx]);
-        int2 *dst = a.chunk[nk & 1] + base;
-        for (uint32_t q = 0; q < nch; q++) dst[q] = make_int2(v, (int)q);
+    }
+    const uint32_t nk = c.k + 1;
+    const uint32_t nx = nk % 3;
+    if (__any_sync(0xffffffffu, n_small > 0)) {
+        uint32_t incl = n_small;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane_id() >= o) incl += t;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (c.st_ns + tot > kStageSmall) stage_flush(c.st_small, c.st_ns, a.small[nk & 1], &a.h->n_small[nx]);
+        uint32_t slot = c.st_ns + incl - n_small;
+#pragma unroll
+        for (int j = 0; j < U; j++)
+            if (newly[j] && cls[j] == 1) c.st_small[slot++] = v[j];
+        c.st_ns += tot;
+    }
+    if (__any_sync(0xffffffffu, n_large > 0)) {
+        // lanes with many chunks (vertices of degree > kDirectChunks*chunk) reserve directly
+        const bool direct = n_large > kDirectChunks;
+        if (__any_sync(0xffffffffu, direct)) {
+            uint32_t slot = warp_reserve(direct ? n_large : 0u, &a.h->n_chunk[nx]);
+            int2 *dst = a.chunk[nk & 1];
+            if (direct) {
+#pragma unroll
+                for (int j = 0; j < U; j++)
+                    for (uint32_t q = 0; q < nch[j]; q++) dst[slot++] = make_int2(v[j], (int)q);
+            }
+        }
+        const uint32_t mine = direct ? 0u : n_large;
+        uint32_t incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane_id() >= o) incl += t;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (tot) {
+            if (c.st_nc + tot > kStageChunk) stage_flush(c.st_chunk, c.st_nc, a.chunk[nk & 1], &a.h->n_chunk[nx]);
+            uint32_t slot = c.st_nc + incl - mine;
+            if (!direct) {
+#pragma unroll
+                for (int j = 0; j < U; j++)
+                    for (uint32_t q = 0; q < nch[j]; q++) c.st_chunk[slot++] = make_int2(v[j], (int)q);
+            }
+            c.st_nc += tot;
+        }
     }
 }
 
@@ -120,41 +212,53 @@ template <typename OffT>
 __device__ __forceinline__ void relax_multi(const GraphArgs<OffT> &a, const bool (&ok)[kUnroll],
                                             const int32_t (&v)[kUnroll], const uint64_t (&cand64)[kUnroll],
                                             SweepCtx &c) {
-    uint32_t dv[kUnroll];
+    unsigned long long kv[kUnroll];
 #pragma unroll
-    for (int j = 0; j < kUnroll; j++) dv[j] = ok[j] ? __ldcg(a.dist + v[j]) : 0u;
-    bool improved[kUnroll];
+    for (int j = 0; j < kUnroll; j++) kv[j] = ok[j] ? __ldcg(a.key + v[j]) : 0ull;
+    bool near[kUnroll], far[kUnroll];
+    uint32_t cls[kUnroll];
+    bool any_far = false;
 #pragma unroll
     for (int j = 0; j < kUnroll; j++) {
-        improved[j] = false;
+        bool improved = false;
+        cls[j] = (uint32_t)kv[j] & 3u;
         if (ok[j]) {
             if (cand64[j] >= (uint64_t)kInf) {
                 set_status(a.h, LLP_ERR_OVERFLOW);
-            } else if ((uint32_t)cand64[j] < dv[j]) {
-                improved[j] = (uint32_t)cand64[j] < atomicMin(a.dist + v[j], (uint32_t)cand64[j]);
+            } else if ((uint32_t)cand64[j] < key_dist(kv[j])) {
+                red_min64(a.key + v[j], (cand64[j] << 32) | cls[j]);
+                improved = true;
             }
         }
-        c.adv += improved[j];
+        c.adv += improved;
+        near[j] = improved && cand64[j] < c.bucket_hi;
+        far[j] = improved && !near[j];
+        any_far |= far[j];
     }
+    if (__any_sync(0xffffffffu, any_far)) {
+        uint32_t cnt = 0, fmin = kInf;
 #pragma unroll
-    for (int j = 0; j < kUnroll; j++) {
-        if (!__any_sync(0xffffffffu, improved[j])) continue;
-        const uint32_t cand = (uint32_t)cand64[j];
-        bool near = improved[j] && (unsigned long long)cand < c.bucket_hi;
-        const bool far = improved[j] && !near;
-        if (__any_sync(0xffffffffu, far)) {
-            const uint32_t slot = warp_append_slot(far, &a.h->n_far[c.fa % 3]);
-            if (far) {
-                if (slot < a.far_cap) {
-                    a.far[c.fa & 1][slot] = make_int2(v[j], (int)cand);
-                    atomicMin(&a.h->far_min[c.fa % 3], cand);
-                } else {
-                    near = true;  // far list full: keep it in the near worklist (still correct)
-                }
-            }
+        for (int j = 0; j < kUnroll; j++) {
+            cnt += far[j];
+            if (far[j]) fmin = min(fmin, (uint32_t)cand64[j]);
         }
-        push_near(a, near, v[j], c);
+        uint32_t slot = warp_reserve(cnt, &a.h->n_far[c.fa % 3]);
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) {
+            if (!far[j]) continue;
+            if (slot < a.far_cap) {
+                a.far[c.fa & 1][slot] = make_int2(v[j], (int)(uint32_t)cand64[j]);
+            } else {
+                near[j] = true;  // far list full: keep it in the near worklist (still correct)
+            }
+            slot++;
+        }
+        if (cnt) atomicMin(&a.h->far_min[c.fa % 3], fmin);
     }
+    bool any_near = false;
+#pragma unroll
+    for (int j = 0; j < kUnroll; j++) any_near |= near[j];
+    if (__any_sync(0xffffffffu, any_near)) push_near(a, near, v, cls, c);
 }
 
 // Expand the out-arcs of up to 32 small vertices (one per lane) edge-balanced
@@ -164,7 +268,7 @@ __device__ __forceinline__ void expand_group(const GraphArgs<OffT> &a, bool vali
     uint32_t du = 0, deg = 0;
     OffT beg = 0;
     if (valid) {
-        du = __ldcg(a.dist + u);
+        du = key_dist(__ldcg(a.key + u));
         beg = __ldg(a.off + u);
         deg = (uint32_t)(__ldg(a.off + u + 1) - beg);
     }
@@ -213,14 +317,16 @@ __device__ __forceinline__ void expand_group(const GraphArgs<OffT> &a, bool vali
 template <typename OffT, bool UNIT>
 __device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item, SweepCtx &c) {
     const int32_t u = item.x;
-    uint32_t su = 0, du = 0;
+    const uint32_t bit = 1u << (u & 31);
+    uint32_t nxt = 0, du = 0;
     if (lane_id() == 0) {
-        su = __ldcg(a.stamp + u);
-        du = __ldcg(a.dist + u);
+        nxt = __ldcg(c.bm_next + (u >> 5));
+        du = key_dist(__ldcg(a.key + u));
+        if (item.y == 0) red_and(c.bm_cur + (u >> 5), ~bit);
     }
-    su = __shfl_sync(0xffffffffu, su, 0);
+    nxt = __shfl_sync(0xffffffffu, nxt, 0);
     du = __shfl_sync(0xffffffffu, du, 0);
-    if ((su >> 2) != c.k) return;  // re-advanced meanwhile: sweep k+1 handles it (warp-uniform)
+    if (nxt & bit) return;  // advanced again meanwhile: sweep k+1 handles it (warp-uniform)
     const OffT b0 = __ldg(a.off + u);
     const OffT e0 = __ldg(a.off + u + 1);
     const OffT beg = b0 + (OffT)item.y * (OffT)a.chunk_edges;
@@ -247,22 +353,80 @@ __device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item
     }
 }
 
-// Adds the CTA's dense_next stamp count to the next sweep's counter.
-__device__ __forceinline__ void flush_stamped(WsHeader *h, SweepCtx &c, uint32_t *s_cnt) {
-    const uint32_t ws = warp_sum(c.stamped);
-    c.stamped = 0;
-    if (lane_id() == 0 && ws) atomicAdd(s_cnt, ws);
+// Dense sweep item: 32 bitmap words (1024 vertices), loaded with one
+// coalesced access; for every non-empty word, its small vertices whose bit is
+// set (and not set again for the next sweep) are expanded, one lane per
+// vertex.  The words are cleared.
+template <typename OffT, bool UNIT>
+__device__ __forceinline__ void scan_words(const GraphArgs<OffT> &a, int64_t g, SweepCtx &c) {
+    const int64_t wi = g * kGroupWords + lane_id();
+    uint32_t act = 0;
+    if (lane_id() < kGroupWords && wi < a.nwords) {
+        const uint32_t b = __ldcg(c.bm_cur + wi);
+        if (b) {
+            c.bm_cur[wi] = 0u;
+            act = b & ~__ldg(&a.cls[wi].y) & ~__ldcg(c.bm_next + wi);
+        }
+    }
+    uint32_t todo = __ballot_sync(0xffffffffu, act != 0);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t word = __shfl_sync(0xffffffffu, act, src);
+        const bool ok = (word >> lane_id()) & 1u;
+        expand_group<OffT, UNIT>(a, ok, (int32_t)((g * kGroupWords + src) * 32 + lane_id()), c);
+    }
+}
+
+// End of a sweep: the CTA publishes every warp's staged list entries with one
+// reservation per list, and adds its dense_next mark count.
+struct BlockFlush {
+    uint32_t ns[16], nc[16];
+    uint32_t base_s, base_c, marked;
+};
+
+template <typename OffT>
+__device__ __forceinline__ void flush_sweep(const GraphArgs<OffT> &a, SweepCtx &c, BlockFlush *bf) {
+    const int wid = threadIdx.x >> 5;
+    const uint32_t nk = c.k + 1, nx = nk % 3;
+    const uint32_t m = warp_sum(c.marked);
+    c.marked = 0;
+    if (lane_id() == 0) {
+        bf->ns[wid] = c.st_ns;
+        bf->nc[wid] = c.st_nc;
+        if (m) atomicAdd(&bf->marked, m);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t t = *s_cnt;
-        *s_cnt = 0;
-        if (t) atomicAdd(&h->n_small[(c.k + 1) % 3], t);
+        uint32_t ts = 0, tc = 0;
+        const int nw = blockDim.x >> 5;
+        for (int i = 0; i < nw; i++) {
+            const uint32_t xs = bf->ns[i], xc = bf->nc[i];
+            bf->ns[i] = ts;
+            bf->nc[i] = tc;
+            ts += xs;
+            tc += xc;
+        }
+        bf->base_s = (ts ? atomicAdd(&a.h->n_small[nx], ts) : 0u);
+        bf->base_c = (tc ? atomicAdd(&a.h->n_chunk[nx], tc) : 0u);
+        if (bf->marked) atomicAdd(&a.h->n_small[nx], bf->marked);
+        bf->marked = 0;
     }
+    __syncthreads();
+    int32_t *ls = a.small[nk & 1] + bf->base_s + bf->ns[wid];
+    for (uint32_t i = lane_id(); i < c.st_ns; i += 32) ls[i] = c.st_small[i];
+    int2 *lc = a.chunk[nk & 1] + bf->base_c + bf->nc[wid];
+    for (uint32_t i = lane_id(); i < c.st_nc; i += 32) lc[i] = c.st_chunk[i];
+    c.st_ns = 0;
+    c.st_nc = 0;
 }
 
 template <typename OffT, bool UNIT>
 __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) {
-    __shared__ uint32_t s_cnt;
+    __shared__ BlockFlush s_flush;
+    __shared__ uint32_t s_work[2];
+    __shared__ int32_t s_stage_small[16][kStageSmall];
+    __shared__ int2 s_stage_chunk[16][kStageChunk];
     WsHeader *h = a.h;
     const long long t0 = globaltimer_ns();
     const long long deadline = t0 + a.deadline_ns;
@@ -272,14 +436,28 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
     const int warps_per_block = blockDim.x >> 5;
     const int64_t gwarp = (int64_t)blockIdx.x * warps_per_block + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
-    if (threadIdx.x == 0) s_cnt = 0;
+    if (threadIdx.x == 0) {
+        s_flush.marked = 0;
+        s_work[0] = 0;
+        s_work[1] = 0;
+    }
 
     // ---- init_global_state / initial_states_to_process (paper Sec. 3.3)
-    for (int64_t v = gtid; v < a.n; v += gthreads) {
-        const uint32_t deg = (uint32_t)(__ldg(a.off + v + 1) - __ldg(a.off + v));
-        const uint32_t cls = deg == 0 ? 0u : (deg <= (uint32_t)a.small_max ? 1u : 2u);
-        a.dist[v] = (v == a.source) ? 0u : kInf;
-        a.stamp[v] = stamp_word((v == a.source && cls) ? 1u : 0u, cls);
+    for (int64_t base = gwarp * 32; base < a.n; base += nwarps * 32) {
+        const int64_t v = base + lane_id();
+        uint32_t deg = 0;
+        if (v < a.n) {
+            deg = (uint32_t)(__ldg(a.off + v + 1) - __ldg(a.off + v));
+            const unsigned long long cl = deg == 0 ? 0ull : (deg <= (uint32_t)a.small_max ? 1ull : 2ull);
+            a.key[v] = ((v == a.source) ? 0ull : ((unsigned long long)kInf << 32)) | cl;
+        }
+        const uint32_t has = __ballot_sync(0xffffffffu, deg > 0);
+        const uint32_t large = __ballot_sync(0xffffffffu, deg > (uint32_t)a.small_max);
+        if (lane_id() == 0) {
+            a.cls[base >> 5] = make_uint2(has, large);
+            a.bm[0][base >> 5] = 0u;
+            a.bm[1][base >> 5] = 0u;
+        }
     }
     if (gtid == 0) {
         h->t_start = t0;
@@ -288,8 +466,12 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
         h->block_cfg_used = a.cfg;
         for (int i = 0; i < 3; i++) h->far_min[i] = kInf;
         h->list_ok[1] = 1;
+    }
+    bool alive = grid_barrier(h, phase, deadline);
+    if (gtid == 0 && alive) {
         const uint32_t src_deg = (uint32_t)(__ldg(a.off + a.source + 1) - __ldg(a.off + a.source));
         if (src_deg > 0) {
+            a.bm[1][a.source >> 5] = 1u << (a.source & 31);
             if (src_deg <= (uint32_t)a.small_max) {
                 a.small[1][0] = a.source;
                 h->n_small[1] = 1;
@@ -300,25 +482,32 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
             }
         }
     }
-    bool alive = grid_barrier(h, phase, deadline);
+    if (alive) alive = grid_barrier(h, phase, deadline);
 
     SweepCtx c;
+    c.st_small = s_stage_small[threadIdx.x >> 5];
+    c.st_chunk = s_stage_chunk[threadIdx.x >> 5];
     c.k = 1;
     c.fa = 0;
     c.bucket_hi = (a.delta == kInf) ? (1ull << 40) : (unsigned long long)a.delta;
     uint32_t dense_sweeps = 0;
     while (alive) {
         const uint32_t k = c.k;
+        c.bm_cur = a.bm[k & 1];
+        c.bm_next = a.bm[(k + 1) & 1];
         const uint32_t ns = *(volatile uint32_t *)&h->n_small[k % 3];
         const uint32_t nc = *(volatile uint32_t *)&h->n_chunk[k % 3];
-        const bool list_ok = *(volatile uint32_t *)&h->list_ok[k % 3] != 0;
-        const bool dense = ns + nc > 0 &&
-                           (!list_ok || a.mode == LLP_MODE_DENSE || (a.mode == LLP_MODE_AUTO && ns > a.dense_thresh));
-        c.dense_next = dense && a.mode != LLP_MODE_SPARSE;
+        const bool dense = *(volatile uint32_t *)&h->list_ok[k % 3] == 0;
+        const unsigned long long arcs = (unsigned long long)ns * (unsigned long long)a.small_max / 2 +
+                                        (unsigned long long)nc * (unsigned long long)a.chunk_edges;
+        c.dense_next = a.mode == LLP_MODE_DENSE || (a.mode == LLP_MODE_AUTO && arcs > a.dense_arcs);
+        if (ns + nc == 0) c.dense_next = false;
+        if (threadIdx.x == 0) s_work[(k + 1) & 1] = 0;  // used after the next grid barrier
         if (gtid == 0) {
             const uint32_t r = (k + 2) % 3;
             h->n_small[r] = 0;
             h->n_chunk[r] = 0;
+            h->work[r] = 0;
             h->list_ok[r] = 0;
             h->list_ok[(k + 1) % 3] = c.dense_next ? 0u : 1u;
             if (k - 1 < kSweepLogCap)
@@ -330,7 +519,6 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
             const uint32_t nf_raw = *(volatile uint32_t *)&h->n_far[c.fa % 3];
             const uint32_t nf = min(nf_raw, a.far_cap);
             if (nf == 0) break;
-            c.dense_next = false;
             const unsigned long long fmin = *(volatile uint32_t *)&h->far_min[c.fa % 3];
             const unsigned long long dl = a.delta;
             unsigned long long nh = (fmin / dl + 1ull) * dl;
@@ -338,7 +526,6 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
             if (gtid == 0) {
                 h->n_far[(c.fa + 2) % 3] = 0;
                 h->far_min[(c.fa + 2) % 3] = kInf;
-                h->list_ok[(k + 1) % 3] = 1;
                 h->aux += 1;
             }
             const int2 *fl = a.far[c.fa & 1];
@@ -349,56 +536,64 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
                 bool live = false;
                 if (ok) {
                     e = fl[i];
-                    live = __ldcg(a.dist + e.x) == (uint32_t)e.y;
+                    live = key_dist(__ldcg(a.key + e.x)) == (uint32_t)e.y;
                 }
-                bool to_near = live && (unsigned long long)(uint32_t)e.y < nh;
-                const bool keep = live && !to_near;
+                bool to_near[1] = {live && (unsigned long long)(uint32_t)e.y < nh};
+                const bool keep = live && !to_near[0];
                 const uint32_t slot = warp_append_slot(keep, &h->n_far[(c.fa + 1) % 3]);
                 if (keep) {
                     if (slot < a.far_cap) {
                         a.far[(c.fa + 1) & 1][slot] = e;
                         atomicMin(&h->far_min[(c.fa + 1) % 3], (uint32_t)e.y);
                     } else {
-                        to_near = true;
+                        to_near[0] = true;
                     }
                 }
-                push_near(a, to_near, e.x, c);
+                const int32_t vv[1] = {e.x};
+                const uint32_t cl[1] = {ok ? (uint32_t)__ldcg(a.key + e.x) & 3u : 0u};
+                push_near(a, to_near, vv, cl, c);
             }
             c.bucket_hi = nh;
             c.fa += 1;
         } else {
             dense_sweeps += dense;
-            const uint32_t ngroups =
-                dense ? (uint32_t)(((int64_t)a.n + 31) / 32) : (uint32_t)(((uint64_t)ns + 31) / 32);
+            // chunks: static round robin (uniform cost, <= chunk_edges arcs)
             const int2 *cl = a.chunk[k & 1];
+            for (int64_t it = gwarp; it < nc; it += nwarps) expand_chunk<OffT, UNIT>(a, cl[it], c);
+            // vertex groups (their cost varies): CTA b owns groups b, b + G, b + 2G, ...
+            // (G = grid size) and its warps take them in turn from a shared counter
+            const uint32_t ngroups = dense ? (uint32_t)(((int64_t)a.nwords + kGroupWords - 1) / kGroupWords)
+                                           : (uint32_t)(((uint64_t)ns + 31) / 32);
             const int32_t *sl = a.small[k & 1];
-            const int64_t total = (int64_t)nc + ngroups;
-            for (int64_t it = gwarp; it < total; it += nwarps) {
-                if (it < nc) {
-                    expand_chunk<OffT, UNIT>(a, cl[it], c);
+            for (;;) {
+                uint32_t j = 0;
+                if (lane_id() == 0) j = atomicAdd(&s_work[k & 1], 1u);
+                j = __shfl_sync(0xffffffffu, j, 0);
+                const uint64_t g64 = (uint64_t)blockIdx.x + (uint64_t)j * gridDim.x;
+                if (g64 >= ngroups) break;
+                const uint32_t g = (uint32_t)g64;
+                if (dense) {
+                    scan_words<OffT, UNIT>(a, g, c);
                 } else {
-                    const int64_t g = it - nc;
-                    int32_t u = 0;
-                    bool ok;
-                    if (dense) {
-                        const int64_t vv = g * 32 + lane_id();
-                        ok = vv < a.n;
-                        u = ok ? (int32_t)vv : 0;
-                        if (ok) ok = __ldcg(a.stamp + u) == stamp_word(k, 1);
-                    } else {
-                        const int64_t i = g * 32 + lane_id();
-                        ok = i < ns;
-                        u = ok ? sl[i] : 0;
-                        if (ok) ok = (__ldcg(a.stamp + u) >> 2) == k;
+                    const int64_t i = (int64_t)g * 32 + lane_id();
+                    bool ok = i < ns;
+                    int32_t u = ok ? sl[i] : 0;
+                    if (ok) {
+                        const uint32_t bit = 1u << (u & 31);
+                        red_and(c.bm_cur + (u >> 5), ~bit);
+                        ok = (__ldcg(c.bm_next + (u >> 5)) & bit) == 0;
                     }
                     expand_group<OffT, UNIT>(a, ok, u, c);
                 }
             }
         }
-        flush_stamped(h, c, &s_cnt);
+        flush_sweep(a, c, &s_flush);
         alive = grid_barrier(h, phase, deadline);
         c.k += 1;
     }
+
+    // ---- final_solution: dist[v] = d(v)
+    for (int64_t v = gtid; v < a.n; v += gthreads) a.dist[v] = key_dist(__ldcg(a.key + v));
 
     // ---- statistics (one atomic per warp)
     const unsigned long long it_s = warp_sum(c.items), ed_s = warp_sum(c.edges), ad_s = warp_sum(c.adv);
@@ -420,7 +615,9 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
 }
 
 struct Layout {
-    uint32_t *stamp;
+    unsigned long long *key;
+    uint2 *cls;
+    uint32_t *bm[2];
     int32_t *small[2];
     int2 *chunk[2];
     int2 *far[2];
@@ -431,10 +628,14 @@ struct Layout {
 Layout carve_graph(void *ws, int32_t n, int64_t m) {
     Carve c(ws);
     Layout L;
+    const size_t nwords = ((size_t)n + 31) / 32;
     // chunks of one sweep: sum over large v of ceil(deg/chunk) <= m/128 + m/17
     const size_t chunk_cap = (size_t)(m / 128 + m / 16 + 2);
     L.far_cap = (uint32_t)std::max<int64_t>(n, 1024);
-    L.stamp = c.take<uint32_t>(n);
+    L.key = c.take<unsigned long long>(n);
+    L.cls = c.take<uint2>(nwords);
+    L.bm[0] = c.take<uint32_t>(nwords);
+    L.bm[1] = c.take<uint32_t>(nwords);
     L.small[0] = c.take<int32_t>(n);
     L.small[1] = c.take<int32_t>(n);
     L.chunk[0] = c.take<int2>(chunk_cap);
@@ -447,7 +648,7 @@ Layout carve_graph(void *ws, int32_t n, int64_t m) {
 
 // Heuristic schedule (the fallback of the learned scheduler).
 void resolve_schedule(const llp_sched_t *s, bool unit, int32_t n, int64_t m, int32_t &mode, uint32_t &delta,
-                      int32_t &cfg, uint32_t &dense_thresh, int &threads) {
+                      int32_t &cfg, unsigned long long &dense_arcs, int &threads) {
     mode = s ? s->mode : LLP_MODE_AUTO;
     if (mode < 0 || mode > 2) mode = LLP_MODE_AUTO;
     delta = s ? s->delta : 0u;
@@ -455,10 +656,11 @@ void resolve_schedule(const llp_sched_t *s, bool unit, int32_t n, int64_t m, int
     if (unit) delta = kInf;         // unit weights: sweeps are BFS levels already
     cfg = s ? s->block_cfg : 0;
     if (cfg < 1 || cfg > LLP_BLOCK_CFGS) cfg = 2;
-    const int pm = (s && s->dense_permille > 0) ? s->dense_permille : 50;
-    dense_thresh = (uint32_t)std::min<int64_t>((int64_t)n * pm / 1000, 0xFFFFFFFFll);
+    // dense sweeps once a sweep touches more than permille/1000 of the arcs
+    const int pm = (s && s->dense_permille > 0) ? s->dense_permille : 20;
+    dense_arcs = (unsigned long long)m * (unsigned long long)pm / 1000ull;
+    (void)n;
     threads = (s && (s->threads == 256 || s->threads == 512)) ? s->threads : 512;
-    (void)m;
 }
 
 template <bool UNIT>
@@ -474,9 +676,10 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
     if (ws_bytes < L.bytes) return LLP_ERR_WORKSPACE_TOO_SMALL;
 
     int32_t mode, cfg;
-    uint32_t delta, dense_thresh;
+    uint32_t delta;
+    unsigned long long dense_arcs;
     int threads;
-    resolve_schedule(s, UNIT, g->n, g->m, mode, delta, cfg, dense_thresh, threads);
+    resolve_schedule(s, UNIT, g->n, g->m, mode, delta, cfg, dense_arcs, threads);
     const BlockCfg bc = block_cfg_of(cfg);
     llp_status_t rc = reset_header(ws, stream);
     if (rc != LLP_OK) return rc;
@@ -487,7 +690,11 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         args.idx = g->indices;
         args.w = UNIT ? nullptr : g->weights;
         args.dist = out;
-        args.stamp = L.stamp;
+        args.nwords = (int32_t)(((int64_t)g->n + 31) / 32);
+        args.key = L.key;
+        args.cls = L.cls;
+        args.bm[0] = L.bm[0];
+        args.bm[1] = L.bm[1];
         args.small[0] = L.small[0];
         args.small[1] = L.small[1];
         args.chunk[0] = L.chunk[0];
@@ -498,7 +705,7 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         args.h = (WsHeader *)ws;
         args.delta = delta;
         args.mode = mode;
-        args.dense_thresh = dense_thresh;
+        args.dense_arcs = dense_arcs;
         args.small_max = bc.small_max;
         args.chunk_edges = bc.chunk;
         args.cfg = cfg;

@@ -99,29 +99,25 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 // Bounded grid-wide barrier for a cooperative (co-resident) grid.  Every block
 // calls it the same number of times.  Returns false when the call must stop
 // (deadline passed or another block aborted); the block then leaves its loop.
-// `phase` is a per-block counter kept in a register/shared by the caller.
+// Sense reversal on one counter word: block 0 adds 2^31 - (gridDim.x - 1), the
+// others add 1, so the word's top bit flips exactly when the last block has
+// arrived (its low bits never change across complete barriers).  Arrival is an
+// acq_rel atomic (it publishes the block's writes, ordered before it by
+// __syncthreads); waiting is an acquire load of the same word.
 __device__ __forceinline__ bool grid_barrier(WsHeader *h, uint32_t &phase, long long deadline) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t target = phase + 1;
-        __threadfence();
-        const uint32_t arrived = atomicAdd(&h->bar_count, 1u) + 1u;
+        const uint32_t add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+        uint32_t old;
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;"
+                     : "=r"(old) : "l"(&h->bar_count), "r"(add) : "memory");
         int ok = 1;
-        if (arrived == gridDim.x) {
-            // the releasing block also enforces the call's total time limit
-            if (globaltimer_ns() > deadline) {
-                set_status(h, LLP_ERR_TIMEOUT);
-                atomicExch(&h->abort_flag, 1u);
-            }
-            atomicExch(&h->bar_count, 0u);
-            __threadfence();
-            st_release_u32(&h->bar_gen, target);
-        } else {
-            uint32_t spins = 0;
-            while (ld_acquire_u32(&h->bar_gen) != target) {
+        uint32_t spins = 0;
+        while (((ld_acquire_u32(&h->bar_count) ^ old) & 0x80000000u) == 0) {
+            if ((++spins & 63u) == 0) {
                 if (ld_relaxed_u32(&h->abort_flag)) { ok = 0; break; }
-                if ((++spins & 255u) == 0 && globaltimer_ns() > deadline) {
+                if (globaltimer_ns() > deadline) {
                     set_status(h, LLP_ERR_TIMEOUT);
                     atomicExch(&h->abort_flag, 1u);
                     ok = 0;
@@ -129,7 +125,10 @@ __device__ __forceinline__ bool grid_barrier(WsHeader *h, uint32_t &phase, long 
                 }
             }
         }
-        __threadfence();
+        if (ok && globaltimer_ns() > deadline) {  // total time limit of the call
+            set_status(h, LLP_ERR_TIMEOUT);
+            atomicExch(&h->abort_flag, 1u);
+        }
         if (ld_relaxed_u32(&h->abort_flag)) ok = 0;
         s_ok = ok;
     }
