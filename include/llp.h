@@ -134,6 +134,31 @@ size_t llp_sssp_workspace_size(int32_t n, int64_t m);
 llp_status_t llp_sssp(const llp_csr_t *g, int32_t source, uint32_t *dist, const llp_sched_t *sched,
                       void *ws, size_t ws_bytes, void *stream);
 
+/* SSSP for callers that cannot allocate device memory.
+ * Same computation and result as llp_sssp, but the scratch space comes from a
+ * fixed 64 MiB array inside this library instead of a caller workspace, so the
+ * caller only provides the graph and dist[].  Meant for code that has no device
+ * allocator of its own or must not call one: a plain C or Fortran client
+ * without a CUDA memory pool, a plugin whose host owns all device memory, or a
+ * latency-critical loop where cudaMalloc's implicit device synchronisation is
+ * not acceptable.  The paper has no counterpart; it is an interface addition.
+ *  - Limit: graphs whose llp_sssp_workspace_size(n, m) exceeds
+ *    llp_sssp_noalloc_max_workspace() (64 MiB; e.g. n = 1M vertices with
+ *    m = 16M arcs fits) are rejected with LLP_ERR_WORKSPACE_TOO_SMALL.
+ *  - The array exists once per GPU that loads the library and stays allocated
+ *    until the process exits.  The first call on a device looks up its device
+ *    address (cudaGetSymbolAddress); make that first call before any stream
+ *    capture on that device.
+ *  - All calls on a device share the one array: calls that overlap on the GPU
+ *    (different streams, or another thread) race and give undefined results.
+ *    Serialise them, e.g. on one stream.
+ *  - llp_get_status()/llp_sweep_log() cannot be pointed at this scratch; the
+ *    device status is not reported (use llp_sssp for diagnostics).
+ *  - Allocates nothing: no cudaMalloc/cudaFree or allocating library call. */
+size_t llp_sssp_noalloc_max_workspace(void);
+llp_status_t llp_sssp_noalloc(const llp_csr_t *g, int32_t source, uint32_t *dist, const llp_sched_t *sched,
+                              void *stream);
+
 /* ------------------------------------------------------------------- BFS
  * Paper Sec. 4.2: G[v] = level; v is forbidden iff an in-neighbour u has
  * G[u] < G[v] - 1; advance sets G[v] = 1 + min G[u].  level[v] = hop distance

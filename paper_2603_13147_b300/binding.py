@@ -299,3 +299,29 @@ def sweep_log(ws: torch.Tensor, stream=None, max_records: int = 4096):
     if cnt < 0:
         raise LlpError(-cnt, "llp_sweep_log")
     return buf[:cnt]
+
+
+def sssp_noalloc_max_workspace() -> int:
+    L = lib()
+    L.llp_sssp_noalloc_max_workspace.restype = ctypes.c_size_t
+    return int(L.llp_sssp_noalloc_max_workspace())
+
+
+def sssp_noalloc(g: DeviceGraph, source: int, out=None, sched: Sched | None = None, stream=None):
+    """SSSP without a caller workspace (the library's fixed 64 MiB scratch array).
+
+    For callers that cannot allocate device memory themselves.  `out` must be
+    given by such callers; when it is None this wrapper creates it with torch,
+    which is for convenience in Python only.  Calls on one device must not
+    overlap on the GPU; the first call on a device must precede any stream
+    capture.  Returns dist (uint32 bit patterns in int32)."""
+    if g.weights is None:
+        raise ValueError("sssp needs weights")
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.int32, device=g.indices.device)
+    _dev(out, torch.int32, "out")
+    c = g.csr()
+    rc = lib().llp_sssp_noalloc(ctypes.byref(c), ctypes.c_int32(source), _ptr(out),
+                                None if sched is None else ctypes.byref(sched), _stream(stream))
+    _check(rc, "llp_sssp_noalloc")
+    return out

@@ -35,6 +35,7 @@
 //     empties.
 // The run stops when no index is forbidden: every worklist is empty.
 #include <algorithm>
+#include <mutex>
 
 #include "llp_common.cuh"
 
@@ -727,9 +728,60 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Scratch for llp_sssp_noalloc: a fixed device array owned by this library.
+// It exists once per GPU that loads the library and stays allocated until the
+// process exits.  Host code must not pass `g_noalloc_scratch` itself to a
+// kernel (on the host that name is only a stand-in for the symbol); the device
+// address is looked up with cudaGetSymbolAddress, once per device.
+constexpr size_t kNoallocScratchBytes = (size_t)64 << 20;  // 64 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64];  // device address of the scratch, per device ordinal
+
+// Returns the device address of the scratch array on the current device,
+// looking it up on first use (must not happen during stream capture).
+llp_status_t noalloc_scratch(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        (void)cudaGetLastError();
+        return LLP_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return LLP_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return LLP_OK;
+}
+
+}  // namespace
 }  // namespace llp
 
 extern "C" {
+
+size_t llp_sssp_noalloc_max_workspace(void) { return llp::kNoallocScratchBytes; }
+
+llp_status_t llp_sssp_noalloc(const llp_csr_t *g, int32_t source, uint32_t *dist, const llp_sched_t *sched,
+                              void *stream) {
+    if (!g || g->n < 1 || g->m < 0) return LLP_ERR_INVALID_ARG;
+    const size_t need = llp::carve_graph(nullptr, g->n, g->m).bytes;
+    if (need > llp::kNoallocScratchBytes) return LLP_ERR_WORKSPACE_TOO_SMALL;
+    void *scratch = nullptr;
+    const llp_status_t rc = llp::noalloc_scratch(&scratch);
+    if (rc != LLP_OK) return rc;
+    return llp::graph_solve<false>(g, source, dist, sched, scratch, llp::kNoallocScratchBytes,
+                                   (cudaStream_t)stream);
+}
 
 size_t llp_sssp_workspace_size(int32_t n, int64_t m) {
     if (n < 1 || m < 0) return 0;
