@@ -219,6 +219,65 @@ size_t llp_reduce_workspace_size(int64_t n);
 llp_status_t llp_reduce(int64_t n, const uint64_t *x, uint64_t *sum, const llp_sched_t *sched, void *ws,
                         size_t ws_bytes, void *stream);
 
+/* ---------------------------------------------------------------- Batched
+ * Many independent instances of three families solved in ONE persistent
+ * launch (plus a one-CTA planning kernel): each CTA takes the next instance
+ * from a device queue, most expensive first, and runs that instance's LLP
+ * sweeps on its own (shared-memory state, CTA barriers).  Results are the same
+ * as the single-instance entry points, bit for bit.  Counts may be 0.  The
+ * *_max_* fields are host-known upper bounds used to size the workspace;
+ * an instance above its bound sets LLP_ERR_INVALID_ARG (device status).
+ * Every call is stream-ordered and capturable in a CUDA graph. */
+typedef struct llp_batch {
+    /* 0-1 knapsack: items of instance i are [knap_item_off[i], knap_item_off[i+1]) of knap_w/knap_v */
+    int32_t knap_count;
+    int32_t knap_max_capacity;
+    const int64_t *knap_item_off; /* [knap_count + 1] */
+    const int32_t *knap_w;
+    const int32_t *knap_v;
+    const int32_t *knap_capacity; /* [knap_count] */
+    int32_t *knap_best;           /* [knap_count] out: optimum of each instance */
+    /* job DAGs: jobs of DAG i are [job_off[i], job_off[i+1]) of the concatenated arrays;
+     * job_succ_offsets (total_jobs + 1 entries) are positions in job_succ_indices, whose
+     * entries are LOCAL job ids of the same DAG */
+    int32_t job_count;
+    int32_t job_max_n;
+    const int64_t *job_off;          /* [job_count + 1] */
+    const int64_t *job_succ_offsets; /* [total_jobs + 1] */
+    const int32_t *job_succ_indices;
+    const int32_t *job_duration;     /* [total_jobs] */
+    int32_t *job_completion;         /* [total_jobs] out */
+    /* stable marriage: instance i has n = sm_n[i]; its n*n preference entries start at
+     * sm_pref_off[i] in sm_men_pref / sm_women_rank (layouts as llp_stable_marriage);
+     * its wife[] output starts at sm_man_off[i] */
+    int32_t sm_count;
+    int32_t sm_max_n;
+    const int32_t *sm_n;
+    const int64_t *sm_pref_off;
+    const int64_t *sm_man_off;
+    const int32_t *sm_men_pref;
+    const int32_t *sm_women_rank;
+    int32_t *sm_wife;
+} llp_batch_t;
+
+/* Launch shape of the batched engine (never changes results); 0 = default. */
+typedef struct llp_batch_cfg {
+    int32_t threads;     /* threads per CTA: 256, 512 or 1024 (default 1024) */
+    int32_t knap_unroll; /* knapsack cells per thread per chunk: 4, 8 (default) or 16 */
+    int32_t reserved[2];
+} llp_batch_cfg_t;
+
+size_t llp_batch_workspace_size(const llp_batch_t *b);
+llp_status_t llp_batch_solve(const llp_batch_t *b, const llp_batch_cfg_t *cfg, const llp_sched_t *sched, void *ws,
+                             size_t ws_bytes, void *stream);
+
+/* Autotuner: runs the batch once untimed and once timed (CUDA events) for every
+ * candidate launch shape and writes the fastest to *best.  Synchronises
+ * `stream`.  h_ms (may be NULL) receives up to max_tried timings; *n_tried the
+ * number of candidates run.  Outputs of the batch hold the last run's result. */
+llp_status_t llp_batch_autotune(const llp_batch_t *b, void *ws, size_t ws_bytes, void *stream,
+                                llp_batch_cfg_t *best, float *h_ms, int32_t max_tried, int32_t *n_tried);
+
 #ifdef __cplusplus
 }
 #endif

@@ -325,3 +325,104 @@ def sssp_noalloc(g: DeviceGraph, source: int, out=None, sched: Sched | None = No
                                 None if sched is None else ctypes.byref(sched), _stream(stream))
     _check(rc, "llp_sssp_noalloc")
     return out
+
+
+# ------------------------------------------------------------------ batched
+
+class Batch(ctypes.Structure):
+    _fields_ = [("knap_count", ctypes.c_int32), ("knap_max_capacity", ctypes.c_int32),
+                ("knap_item_off", ctypes.c_void_p), ("knap_w", ctypes.c_void_p), ("knap_v", ctypes.c_void_p),
+                ("knap_capacity", ctypes.c_void_p), ("knap_best", ctypes.c_void_p),
+                ("job_count", ctypes.c_int32), ("job_max_n", ctypes.c_int32),
+                ("job_off", ctypes.c_void_p), ("job_succ_offsets", ctypes.c_void_p),
+                ("job_succ_indices", ctypes.c_void_p), ("job_duration", ctypes.c_void_p),
+                ("job_completion", ctypes.c_void_p),
+                ("sm_count", ctypes.c_int32), ("sm_max_n", ctypes.c_int32),
+                ("sm_n", ctypes.c_void_p), ("sm_pref_off", ctypes.c_void_p), ("sm_man_off", ctypes.c_void_p),
+                ("sm_men_pref", ctypes.c_void_p), ("sm_women_rank", ctypes.c_void_p), ("sm_wife", ctypes.c_void_p)]
+
+
+class BatchCfg(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("knap_unroll", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
+class DeviceBatch:
+    """Device-resident batch of knapsack / job-DAG / stable-marriage instances
+    (host dicts as produced by synth.knapsack_batch / job_batch / marriage_batch)."""
+
+    def __init__(self, knap=None, job=None, sm=None, device="cuda"):
+        import numpy as np
+        d = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(device)
+        self.device = device
+        self.t = {}
+        self.knap_count = self.job_count = self.sm_count = 0
+        self.knap_max_capacity = self.job_max_n = self.sm_max_n = 0
+        if knap is not None and knap["count"] > 0:
+            self.knap_count = int(knap["count"])
+            self.knap_max_capacity = int(knap["capacity"].max())
+            self.t.update(knap_item_off=d(knap["item_off"], np.int64), knap_w=d(knap["w"], np.int32),
+                          knap_v=d(knap["v"], np.int32), knap_capacity=d(knap["capacity"], np.int32),
+                          knap_best=torch.empty(self.knap_count, dtype=torch.int32, device=device))
+        if job is not None and job["count"] > 0:
+            self.job_count = int(job["count"])
+            self.job_max_n = int(np.diff(job["job_off"]).max())
+            self.t.update(job_off=d(job["job_off"], np.int64), job_succ_offsets=d(job["succ_offsets"], np.int64),
+                          job_succ_indices=d(job["succ_indices"], np.int32),
+                          job_duration=d(job["duration"], np.int32),
+                          job_completion=torch.empty(int(job["job_off"][-1]), dtype=torch.int32, device=device))
+        if sm is not None and sm["count"] > 0:
+            self.sm_count = int(sm["count"])
+            self.sm_max_n = int(sm["n"].max())
+            man_off = np.zeros(self.sm_count + 1, np.int64)
+            man_off[1:] = np.cumsum(sm["n"])
+            self.sm_man_off_host = man_off
+            self.t.update(sm_n=d(sm["n"], np.int32), sm_pref_off=d(sm["pref_off"], np.int64),
+                          sm_man_off=d(man_off, np.int64), sm_men_pref=d(sm["men_pref"], np.int32),
+                          sm_women_rank=d(sm["women_rank"], np.int32),
+                          sm_wife=torch.empty(int(man_off[-1]), dtype=torch.int32, device=device))
+
+    def struct(self) -> Batch:
+        b = Batch()
+        b.knap_count, b.knap_max_capacity = self.knap_count, self.knap_max_capacity
+        b.job_count, b.job_max_n = self.job_count, self.job_max_n
+        b.sm_count, b.sm_max_n = self.sm_count, self.sm_max_n
+        for k, v in self.t.items():
+            setattr(b, k, v.data_ptr())
+        return b
+
+    @property
+    def count(self):
+        return self.knap_count + self.job_count + self.sm_count
+
+
+def batch_workspace_size(db: DeviceBatch) -> int:
+    L = lib()
+    L.llp_batch_workspace_size.restype = ctypes.c_size_t
+    b = db.struct()
+    return int(L.llp_batch_workspace_size(ctypes.byref(b)))
+
+
+def batch_solve(db: DeviceBatch, cfg: BatchCfg | None = None, sched=None, ws=None, stream=None):
+    """Solves every instance of the batch in one persistent launch.  Returns the workspace."""
+    if ws is None:
+        ws = workspace(batch_workspace_size(db), db.device)
+    b = db.struct()
+    rc = lib().llp_batch_solve(ctypes.byref(b), None if cfg is None else ctypes.byref(cfg),
+                               None if sched is None else ctypes.byref(sched), _ptr(ws), ctypes.c_size_t(ws.numel()),
+                               _stream(stream))
+    _check(rc, "llp_batch_solve")
+    return ws
+
+
+def batch_autotune(db: DeviceBatch, ws=None, stream=None):
+    """Times every candidate launch shape; returns (best BatchCfg, list of ms, workspace)."""
+    if ws is None:
+        ws = workspace(batch_workspace_size(db), db.device)
+    b = db.struct()
+    best = BatchCfg()
+    ms = (ctypes.c_float * 16)()
+    n = ctypes.c_int32(0)
+    rc = lib().llp_batch_autotune(ctypes.byref(b), _ptr(ws), ctypes.c_size_t(ws.numel()), _stream(stream),
+                                  ctypes.byref(best), ms, ctypes.c_int32(16), ctypes.byref(n))
+    _check(rc, "llp_batch_autotune")
+    return best, [float(ms[i]) for i in range(n.value)], ws

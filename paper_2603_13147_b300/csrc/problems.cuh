@@ -129,3 +129,100 @@ __device__ __forceinline__ long long cta_sum_i32(int32_t n, const int32_t *v) {
 }
 
 }  // namespace llp
+
+namespace llp {
+
+// ------------------------------------------------------------ job scheduling
+// Paper Sec. 4.4 on one CTA.  off[0..n] are the job rows' arc positions (in
+// the caller's concatenated successor array), idx[] local successor ids in
+// [0, n).  maxp/remaining/list0/list1 are CTA-private (shared or global).
+// Level-synchronous: a job enters the worklist when its last predecessor is
+// fixed, is advanced to maxp + t and fixed, and publishes to its successors.
+// Returns the number of fixed jobs (< n means a cycle).
+__device__ __forceinline__ int32_t job_cta(int32_t n, const int64_t *off, const int32_t *idx, const int32_t *dur,
+                                           int32_t *completion, int32_t *maxp, int32_t *remaining, int32_t *list0,
+                                           int32_t *list1, WsHeader *h) {
+    __shared__ int32_t s_cnt[2];
+    __shared__ int32_t s_fixed;
+    const int T = blockDim.x;
+    for (int32_t j = threadIdx.x; j < n; j += T) {
+        maxp[j] = 0;
+        remaining[j] = 0;
+    }
+    if (threadIdx.x == 0) {
+        s_cnt[0] = 0;
+        s_cnt[1] = 0;
+        s_fixed = 0;
+    }
+    __syncthreads();
+    const int64_t e0 = off[0], e1 = off[n];
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += T) {
+        const int32_t s = __ldg(idx + e);
+        if ((uint32_t)s < (uint32_t)n) atomicAdd(remaining + s, 1);
+        else set_status(h, LLP_ERR_INVALID_ARG);
+    }
+    __syncthreads();
+    for (int32_t j = threadIdx.x; j < n; j += T)
+        if (remaining[j] == 0) list0[atomicAdd(&s_cnt[0], 1)] = j;
+    __syncthreads();
+    int cur = 0;
+    int32_t fixed_local = 0;
+    for (;;) {
+        const int32_t cnt = s_cnt[cur];
+        if (cnt == 0) break;
+        const int32_t *L = cur ? list1 : list0;
+        int32_t *N = cur ? list0 : list1;
+        for (int32_t i = threadIdx.x; i < cnt; i += T) {
+            const int32_t j = L[i];
+            long long c = (long long)maxp[j] + __ldg(dur + j);
+            if (c > 0x7FFFFFFFll) {
+                set_status(h, LLP_ERR_OVERFLOW);
+                c = 0x7FFFFFFF;
+            }
+            completion[j] = (int32_t)c;
+            fixed_local++;
+            for (int64_t e = off[j]; e < off[j + 1]; e++) {
+                const int32_t s = __ldg(idx + e);
+                atomicMax(maxp + s, (int32_t)c);
+                if (atomicSub(remaining + s, 1) == 1) N[atomicAdd(&s_cnt[cur ^ 1], 1)] = s;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_cnt[cur] = 0;
+        cur ^= 1;
+        __syncthreads();
+    }
+    atomicAdd(&s_fixed, fixed_local);
+    __syncthreads();
+    const int32_t fixed = s_fixed;
+    __syncthreads();
+    return fixed;
+}
+
+// ------------------------------------------------------- stable marriage CTA
+// Paper Sec. 4.3 on one CTA: best[] and next[] CTA-private (shared memory for
+// n <= a few thousand).  Threads take men in turn and carry displacement
+// chains to their end (propose_chain).  Writes wife[m].  Returns proposals.
+__device__ __forceinline__ unsigned long long marriage_cta(int32_t n, const int32_t *men_pref,
+                                                           const int32_t *women_rank, int32_t *wife,
+                                                           unsigned long long *best, int32_t *next, WsHeader *h,
+                                                           long long deadline) {
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        best[i] = kEmptySuitor;
+        next[i] = 0;
+    }
+    __syncthreads();
+    unsigned long long props = 0;
+    bool failed = false;
+    for (int32_t m = threadIdx.x; m < n && !failed; m += blockDim.x)
+        props += propose_chain(m, 0, n, men_pref, women_rank, best, next, h, deadline, failed);
+    __syncthreads();
+    for (int32_t m = threadIdx.x; m < n; m += blockDim.x) {
+        const int32_t k = next[m];
+        wife[m] = (k >= 0 && k < n) ? __ldg(men_pref + (int64_t)m * n + k) : -1;
+    }
+    __syncthreads();
+    return props;
+}
+
+}  // namespace llp
