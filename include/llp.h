@@ -278,6 +278,46 @@ llp_status_t llp_batch_solve(const llp_batch_t *b, const llp_batch_cfg_t *cfg, c
 llp_status_t llp_batch_autotune(const llp_batch_t *b, void *ws, size_t ws_bytes, void *stream,
                                 llp_batch_cfg_t *best, float *h_ms, int32_t max_tried, int32_t *n_tried);
 
+/* ------------------------------------------------------ Learned scheduler
+ * Not in the paper (its conclusion asks for an adaptive runtime choice of
+ * solver): a small fp32 MLP maps instance features of a graph to a schedule
+ * of the graph sweep.  Setting llp_sched_t.use_mlp = 1 and mlp_params makes
+ * llp_sssp / llp_bfs run a feature kernel and an inference kernel on the device
+ * before the sweep, which then uses the chosen schedule.  Results never depend
+ * on the schedule.  The scheduler network is features(16) -> 64 -> 64 -> 14
+ * logits = heads {mode: 3 (AUTO, SPARSE, DENSE), bucket-width class: 8
+ * (0 = none, c >= 1: width = max sampled weight * 2^(c-3)), block_cfg: 3}.
+ * Parameters: one fp32 vector, row-major W1[F,H1] b1 W2[H1,H2] b2 W3[H2,O] b3. */
+typedef struct llp_mlp_dims {
+    int32_t F, H1, H2, O; /* each 1..128 */
+    int32_t nheads;       /* 1..8, sum of heads[] == O */
+    int32_t heads[8];
+} llp_mlp_dims_t;
+
+size_t llp_mlp_param_count(const llp_mlp_dims_t *dims);
+size_t llp_mlp_workspace_size(const llp_mlp_dims_t *dims, int32_t batch);
+
+/* logits[batch, O] = MLP(X[batch, F]).  All device pointers. */
+llp_status_t llp_mlp_forward(const llp_mlp_dims_t *dims, const float *params, const float *X, int32_t batch,
+                             float *logits, void *stream);
+
+/* loss[0] = mean over the batch of the sum over heads of the softmax
+ * cross-entropy with labels Y[batch, nheads] (class index within each head; a
+ * label outside its head contributes nothing); grad = d loss / d params (same
+ * layout as params).  The gradient reduction is deterministic. */
+llp_status_t llp_mlp_loss_grad(const llp_mlp_dims_t *dims, const float *params, const float *X, const int32_t *Y,
+                               int32_t batch, float *loss, float *grad, void *ws, size_t ws_bytes, void *stream);
+
+/* One Adam step (Kingma and Ba 2015) in place; step >= 1. */
+llp_status_t llp_mlp_adam(float *params, const float *grad, float *m, float *v, size_t n, int32_t step, float lr,
+                          float beta1, float beta2, float eps, void *stream);
+
+/* Runs only the feature and inference kernels for graph g (the default
+ * 16-64-64-14 network) into the header of ws.  If h_chosen / h_features are not
+ * NULL, synchronises the stream and copies the choice / the 16 features out. */
+llp_status_t llp_graph_schedule(const llp_csr_t *g, int32_t source, int32_t unit_weights, const float *params,
+                                void *ws, size_t ws_bytes, void *stream, llp_sched_t *h_chosen, float *h_features);
+
 #ifdef __cplusplus
 }
 #endif

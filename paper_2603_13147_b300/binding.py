@@ -426,3 +426,74 @@ def batch_autotune(db: DeviceBatch, ws=None, stream=None):
                                   ctypes.byref(best), ms, ctypes.c_int32(16), ctypes.byref(n))
     _check(rc, "llp_batch_autotune")
     return best, [float(ms[i]) for i in range(n.value)], ws
+
+
+# -------------------------------------------------------- learned scheduler
+
+class MlpDims(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_int32), ("H1", ctypes.c_int32), ("H2", ctypes.c_int32), ("O", ctypes.c_int32),
+                ("nheads", ctypes.c_int32), ("heads", ctypes.c_int32 * 8)]
+
+
+SCHED_F, SCHED_H1, SCHED_H2 = 16, 64, 64
+SCHED_HEADS = (3, 8, 3)  # mode, bucket-width class, block_cfg
+
+
+def mlp_dims(F=SCHED_F, H1=SCHED_H1, H2=SCHED_H2, heads=SCHED_HEADS) -> MlpDims:
+    d = MlpDims()
+    d.F, d.H1, d.H2, d.O, d.nheads = F, H1, H2, sum(heads), len(heads)
+    for i, h in enumerate(heads):
+        d.heads[i] = h
+    return d
+
+
+def mlp_param_count(d: MlpDims) -> int:
+    L = lib()
+    L.llp_mlp_param_count.restype = ctypes.c_size_t
+    return int(L.llp_mlp_param_count(ctypes.byref(d)))
+
+
+def mlp_forward(d: MlpDims, params: torch.Tensor, X: torch.Tensor, stream=None) -> torch.Tensor:
+    _dev(params, torch.float32, "params"); _dev(X, torch.float32, "X")
+    out = torch.empty((X.shape[0], d.O), dtype=torch.float32, device=X.device)
+    rc = lib().llp_mlp_forward(ctypes.byref(d), _ptr(params), _ptr(X), ctypes.c_int32(X.shape[0]), _ptr(out),
+                               _stream(stream))
+    _check(rc, "llp_mlp_forward")
+    return out
+
+
+def mlp_loss_grad(d: MlpDims, params: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, ws=None, stream=None):
+    """Returns (loss tensor[1], grad tensor like params, workspace)."""
+    _dev(params, torch.float32, "params"); _dev(X, torch.float32, "X"); _dev(Y, torch.int32, "Y")
+    L = lib()
+    L.llp_mlp_workspace_size.restype = ctypes.c_size_t
+    B = X.shape[0]
+    if ws is None:
+        ws = workspace(L.llp_mlp_workspace_size(ctypes.byref(d), ctypes.c_int32(B)), X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    grad = torch.empty_like(params)
+    rc = L.llp_mlp_loss_grad(ctypes.byref(d), _ptr(params), _ptr(X), _ptr(Y), ctypes.c_int32(B), _ptr(loss),
+                             _ptr(grad), _ptr(ws), ctypes.c_size_t(ws.numel()), _stream(stream))
+    _check(rc, "llp_mlp_loss_grad")
+    return loss, grad, ws
+
+
+def mlp_adam(params, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    rc = lib().llp_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), ctypes.c_size_t(params.numel()),
+                            ctypes.c_int32(step), ctypes.c_float(lr), ctypes.c_float(beta1), ctypes.c_float(beta2),
+                            ctypes.c_float(eps), _stream(stream))
+    _check(rc, "llp_mlp_adam")
+
+
+def graph_schedule(g: DeviceGraph, source: int, params: torch.Tensor, unit_weights=False, ws=None, stream=None):
+    """Runs the device feature + inference kernels; returns (chosen Sched, features list)."""
+    if ws is None:
+        ws = workspace(1 << 16, g.indices.device)
+    chosen = Sched()
+    feats = (ctypes.c_float * 16)()
+    c = g.csr()
+    rc = lib().llp_graph_schedule(ctypes.byref(c), ctypes.c_int32(source), ctypes.c_int32(1 if unit_weights else 0),
+                                  _ptr(params), _ptr(ws), ctypes.c_size_t(ws.numel()), _stream(stream),
+                                  ctypes.byref(chosen), feats)
+    _check(rc, "llp_graph_schedule")
+    return chosen, [float(x) for x in feats]

@@ -40,6 +40,10 @@
 #include "llp_common.cuh"
 
 namespace llp {
+
+llp_status_t enqueue_learned_schedule(const llp_csr_t *g, int32_t source, bool unit, const float *params,
+                                      WsHeader *h, cudaStream_t st);
+
 namespace {
 
 struct BlockCfg {
@@ -79,10 +83,14 @@ struct GraphArgs {
     int32_t small_max;
     int32_t chunk_edges;
     int32_t cfg;
+    int32_t use_dev_sched;  // 1: take mode/delta/cfg from the header (learned scheduler)
     long long deadline_ns;
 };
 
 struct SweepCtx {
+    // schedule of this run (from the arguments, or chosen on the device)
+    int32_t mode, cfg, small_max, chunk_edges;
+    uint32_t delta;
     uint32_t k;                    // current sweep
     unsigned long long bucket_hi;  // exclusive bound of the current bucket
     uint32_t fa;                   // far-list generation
@@ -153,7 +161,7 @@ __device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, const bool (
         n_small += (newly[j] && cls[j] == 1);
         if (newly[j] && cls[j] == 2) {
             const uint32_t deg = (uint32_t)(__ldg(a.off + v[j] + 1) - __ldg(a.off + v[j]));
-            nch[j] = (deg + a.chunk_edges - 1) / a.chunk_edges;
+            nch[j] = (deg + c.chunk_edges - 1) / c.chunk_edges;
             n_large += nch[j];
         }
     }
@@ -330,8 +338,8 @@ __device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item
     if (nxt & bit) return;  // advanced again meanwhile: sweep k+1 handles it (warp-uniform)
     const OffT b0 = __ldg(a.off + u);
     const OffT e0 = __ldg(a.off + u + 1);
-    const OffT beg = b0 + (OffT)item.y * (OffT)a.chunk_edges;
-    const OffT end = min(e0, beg + (OffT)a.chunk_edges);
+    const OffT beg = b0 + (OffT)item.y * (OffT)c.chunk_edges;
+    const OffT end = min(e0, beg + (OffT)c.chunk_edges);
     c.items += (lane_id() == 0 && item.y == 0);
     c.edges += (lane_id() == 0) ? (unsigned long long)(end - beg) : 0ull;
     for (OffT base = beg; base < end; base += 32 * kUnroll) {
@@ -443,17 +451,35 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
         s_work[1] = 0;
     }
 
+    SweepCtx c;
+    c.mode = a.mode;
+    c.delta = a.delta;
+    c.cfg = a.cfg;
+    if (a.use_dev_sched && *(volatile int32_t *)&h->sched_valid) {
+        c.mode = *(volatile int32_t *)&h->sched_mode;
+        c.delta = *(volatile uint32_t *)&h->sched_delta;
+        c.cfg = *(volatile int32_t *)&h->sched_cfg;
+        if (c.mode < 0 || c.mode > 2) c.mode = LLP_MODE_AUTO;
+        if (c.cfg < 1 || c.cfg > LLP_BLOCK_CFGS) c.cfg = 2;
+        if (UNIT) c.delta = kInf;
+    }
+    {
+        const BlockCfg bcfg = block_cfg_of(c.cfg);
+        c.small_max = bcfg.small_max;
+        c.chunk_edges = bcfg.chunk;
+    }
+
     // ---- init_global_state / initial_states_to_process (paper Sec. 3.3)
     for (int64_t base = gwarp * 32; base < a.n; base += nwarps * 32) {
         const int64_t v = base + lane_id();
         uint32_t deg = 0;
         if (v < a.n) {
             deg = (uint32_t)(__ldg(a.off + v + 1) - __ldg(a.off + v));
-            const unsigned long long cl = deg == 0 ? 0ull : (deg <= (uint32_t)a.small_max ? 1ull : 2ull);
+            const unsigned long long cl = deg == 0 ? 0ull : (deg <= (uint32_t)c.small_max ? 1ull : 2ull);
             a.key[v] = ((v == a.source) ? 0ull : ((unsigned long long)kInf << 32)) | cl;
         }
         const uint32_t has = __ballot_sync(0xffffffffu, deg > 0);
-        const uint32_t large = __ballot_sync(0xffffffffu, deg > (uint32_t)a.small_max);
+        const uint32_t large = __ballot_sync(0xffffffffu, deg > (uint32_t)c.small_max);
         if (lane_id() == 0) {
             a.cls[base >> 5] = make_uint2(has, large);
             a.bm[0][base >> 5] = 0u;
@@ -462,9 +488,9 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
     }
     if (gtid == 0) {
         h->t_start = t0;
-        h->mode_used = a.mode;
-        h->delta_used = a.delta;
-        h->block_cfg_used = a.cfg;
+        h->mode_used = c.mode;
+        h->delta_used = c.delta;
+        h->block_cfg_used = c.cfg;
         for (int i = 0; i < 3; i++) h->far_min[i] = kInf;
         h->list_ok[1] = 1;
     }
@@ -473,11 +499,11 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
         const uint32_t src_deg = (uint32_t)(__ldg(a.off + a.source + 1) - __ldg(a.off + a.source));
         if (src_deg > 0) {
             a.bm[1][a.source >> 5] = 1u << (a.source & 31);
-            if (src_deg <= (uint32_t)a.small_max) {
+            if (src_deg <= (uint32_t)c.small_max) {
                 a.small[1][0] = a.source;
                 h->n_small[1] = 1;
             } else {
-                const uint32_t nch = (src_deg + a.chunk_edges - 1) / a.chunk_edges;
+                const uint32_t nch = (src_deg + c.chunk_edges - 1) / c.chunk_edges;
                 for (uint32_t q = 0; q < nch; q++) a.chunk[1][q] = make_int2(a.source, (int)q);
                 h->n_chunk[1] = nch;
             }
@@ -485,12 +511,11 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
     }
     if (alive) alive = grid_barrier(h, phase, deadline);
 
-    SweepCtx c;
     c.st_small = s_stage_small[threadIdx.x >> 5];
     c.st_chunk = s_stage_chunk[threadIdx.x >> 5];
     c.k = 1;
     c.fa = 0;
-    c.bucket_hi = (a.delta == kInf) ? (1ull << 40) : (unsigned long long)a.delta;
+    c.bucket_hi = (c.delta == kInf) ? (1ull << 40) : (unsigned long long)c.delta;
     uint32_t dense_sweeps = 0;
     while (alive) {
         const uint32_t k = c.k;
@@ -499,9 +524,9 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
         const uint32_t ns = *(volatile uint32_t *)&h->n_small[k % 3];
         const uint32_t nc = *(volatile uint32_t *)&h->n_chunk[k % 3];
         const bool dense = *(volatile uint32_t *)&h->list_ok[k % 3] == 0;
-        const unsigned long long arcs = (unsigned long long)ns * (unsigned long long)a.small_max / 2 +
-                                        (unsigned long long)nc * (unsigned long long)a.chunk_edges;
-        c.dense_next = a.mode == LLP_MODE_DENSE || (a.mode == LLP_MODE_AUTO && arcs > a.dense_arcs);
+        const unsigned long long arcs = (unsigned long long)ns * (unsigned long long)c.small_max / 2 +
+                                        (unsigned long long)nc * (unsigned long long)c.chunk_edges;
+        c.dense_next = c.mode == LLP_MODE_DENSE || (c.mode == LLP_MODE_AUTO && arcs > a.dense_arcs);
         if (ns + nc == 0) c.dense_next = false;
         if (threadIdx.x == 0) s_work[(k + 1) & 1] = 0;  // used after the next grid barrier
         if (gtid == 0) {
@@ -521,7 +546,7 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
             const uint32_t nf = min(nf_raw, a.far_cap);
             if (nf == 0) break;
             const unsigned long long fmin = *(volatile uint32_t *)&h->far_min[c.fa % 3];
-            const unsigned long long dl = a.delta;
+            const unsigned long long dl = c.delta;
             unsigned long long nh = (fmin / dl + 1ull) * dl;
             if (nh < c.bucket_hi + dl) nh = c.bucket_hi + dl;
             if (gtid == 0) {
@@ -684,6 +709,11 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
     const BlockCfg bc = block_cfg_of(cfg);
     llp_status_t rc = reset_header(ws, stream);
     if (rc != LLP_OK) return rc;
+    const bool learned = s && s->use_mlp && s->mlp_params;
+    if (learned) {
+        rc = enqueue_learned_schedule(g, source, UNIT, s->mlp_params, (WsHeader *)ws, stream);
+        if (rc != LLP_OK) return rc;
+    }
 
     auto fill = [&](auto &args) {
         args.n = g->n;
@@ -710,6 +740,7 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         args.small_max = bc.small_max;
         args.chunk_edges = bc.chunk;
         args.cfg = cfg;
+        args.use_dev_sched = learned ? 1 : 0;
         args.deadline_ns = deadline_from(s);
     };
     if (g->offsets_64) {

@@ -56,6 +56,13 @@ struct alignas(256) WsHeader {
     uint32_t far_min[3];
     uint32_t list_ok[3];
     uint32_t scratch[16];
+    // ---- schedule chosen on the device by the learned scheduler (graph engine)
+    int32_t sched_mode;
+    uint32_t sched_delta;
+    int32_t sched_cfg;
+    int32_t sched_valid;
+    float feat[16];  // instance features the choice was made from
+    float feat_wmax; // largest sampled arc weight
 };
 static_assert(sizeof(WsHeader) <= kHeaderZeroBytes, "header too large");
 
