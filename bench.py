@@ -14,6 +14,7 @@ instead, on the same graph, as the reference arm.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -272,6 +273,10 @@ def run_gpu(args):
         "clocks": clocks.summary(),
         "wall_s_timed": t_wall,
     }
+    if not args.no_batched:
+        line["batched"] = bench_batched(llp, dev, stream)
+    if not args.no_learned:
+        line["learned"] = bench_learned(llp, dev, g, s)
     if rank == 0 and not args.no_cpu_baseline:
         gt, dt, dref = cpu_oracle_sample(g, s)
         line["cpu_baseline"] = {"value": gt, "unit": "GTEPS", "cores": 1, "kind": "oracle",
@@ -285,6 +290,137 @@ def run_gpu(args):
     return 0
 
 
+def _ev_time(fn, reps=3, stream=None):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def bench_batched(llp, dev, stream):
+    """Batched workload (4,096 knapsack + 2,048 job DAGs + 1,024 stable marriages): one
+    persistent launch, autotuned launch shape, replayed from a CUDA graph, against the
+    plain engine called once per instance on the same stream (timed on a sample of
+    every family and scaled to the full counts)."""
+    import torch
+    import synth
+    knap = synth.knapsack_batch()
+    job = synth.job_batch()
+    sm = synth.marriage_batch()
+    db = llp.DeviceBatch(knap, job, sm, device=dev)
+    ws = llp.workspace(llp.batch_workspace_size(db), dev)
+    cfg, tune_ms, ws = llp.batch_autotune(db, ws=ws, stream=stream)
+    st = torch.cuda.Stream(dev)
+    with torch.cuda.stream(st):
+        llp.batch_solve(db, cfg, ws=ws, stream=st)
+    st.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        llp.batch_solve(db, cfg, ws=ws, stream=st)
+    batched_ms = _ev_time(graph.replay, reps=3)
+    bst = llp.get_status(ws)
+    total = db.count
+
+    # plain engine: one single-instance call per instance (sampled per family)
+    wk = torch.from_numpy(knap["w"]).to(dev)
+    vk = torch.from_numpy(knap["v"]).to(dev)
+    wsk = llp.workspace(llp.lib().llp_knapsack_workspace_size(ctypes.c_int32(0), ctypes.c_int32(65536)) + (1 << 20), dev)
+    best = torch.empty(1, dtype=torch.int32, device=dev)
+    kidx = np.arange(0, knap["count"], 16)
+
+    def plain_knap():
+        for i in kidx:
+            a, b = int(knap["item_off"][i]), int(knap["item_off"][i + 1])
+            llp.knapsack(wk[a:b], vk[a:b], int(knap["capacity"][i]), want_row=False, ws=wsk)
+    t_knap = _ev_time(plain_knap, reps=1) * knap["count"] / len(kidx)
+    jidx = np.arange(0, job["count"], 8)
+    jgraphs = []
+    for i in jidx:
+        j0, j1 = int(job["job_off"][i]), int(job["job_off"][i + 1])
+        off = job["succ_offsets"][j0:j1 + 1] - job["succ_offsets"][j0]
+        ind = job["succ_indices"][job["succ_offsets"][j0]:job["succ_offsets"][j1]]
+        gj = llp.DeviceGraph.from_host(dict(n=j1 - j0, m=len(ind), offsets=off, indices=ind, weights=None), dev)
+        jgraphs.append((gj, torch.from_numpy(job["duration"][j0:j1]).to(dev)))
+    wsj = llp.workspace(llp.lib().llp_job_schedule_workspace_size(ctypes.c_int32(8192), ctypes.c_int64(0)), dev)
+
+    def plain_job():
+        for gj, dj in jgraphs:
+            llp.job_schedule(gj, dj, ws=wsj)
+    t_job = _ev_time(plain_job, reps=1) * job["count"] / len(jidx)
+    sidx = np.arange(0, sm["count"], 8)
+    sins = []
+    for i in sidx:
+        n = int(sm["n"][i]); p0 = int(sm["pref_off"][i])
+        sins.append((torch.from_numpy(sm["men_pref"][p0:p0 + n * n].reshape(n, n)).to(dev),
+                     torch.from_numpy(sm["women_rank"][p0:p0 + n * n].reshape(n, n)).to(dev)))
+    wss = llp.workspace(llp.lib().llp_stable_marriage_workspace_size(ctypes.c_int32(1024)), dev)
+
+    def plain_sm():
+        for a_, b_ in sins:
+            llp.stable_marriage(a_, b_, ws=wss, want_husband=False, want_next=False)
+    t_sm = _ev_time(plain_sm, reps=1) * sm["count"] / len(sidx)
+    plain_ms = t_knap + t_job + t_sm
+    return {"metric": "instances/s", "instances": total, "batched_ms": batched_ms,
+            "batched_inst_per_s": total / (batched_ms * 1e-3), "plain_ms_est": plain_ms,
+            "plain_inst_per_s": total / (plain_ms * 1e-3), "speedup": plain_ms / batched_ms,
+            "plain_family_ms_est": {"knapsack": t_knap, "job": t_job, "marriage": t_sm},
+            "plain_sample": "every 16th knapsack, 8th job DAG and 8th marriage instance, scaled",
+            "cfg": {"threads": cfg.threads, "knap_unroll": cfg.knap_unroll}, "autotune_ms": tune_ms,
+            "status": bst["status"], "cuda_graph": True}
+
+
+def bench_learned(llp, dev, g22, s22):
+    """Mixed stream: R-MAT scale 20/22/24 SSSP, 2048x2048 grid SSSP, closure of a random
+    DAG (n=8192, p=4/n).  Learned schedule (network on the device) against the fixed
+    heuristic schedule of the plain engine; end-to-end device time of the stream."""
+    import torch
+    import synth
+    from paper_2603_13147_b300 import sched as S
+    if not os.path.exists(S.MODEL_PATH):
+        return {"unavailable": "no trained scheduler model in the package"}
+    params = S.load_model(device=dev)
+    items = []
+    for scale in (20, 22, 24):
+        gg = g22 if scale == 22 else synth.rmat(scale, seed=6 + scale)
+        src = s22 if scale == 22 else synth.max_out_degree_vertex(gg)
+        items.append((f"rmat{scale}_sssp", gg, src))
+    items.append(("grid2048_sssp", synth.grid_graph(2048, 2048, 1, 1000, seed=6), 0))
+    res = {}
+    tot_h = tot_l = 0.0
+    for name, gg, src in items:
+        dg = llp.DeviceGraph.from_host(gg, dev)
+        ws = llp.workspace(llp.sssp_workspace_size(gg["n"], gg["m"]), dev)
+        out = torch.empty(gg["n"], dtype=torch.int32, device=dev)
+        th = _ev_time(lambda: llp.sssp(dg, src, out=out, ws=ws), reps=3)
+        ref = out.clone()
+        ls = S.learned_sched(params)
+        tl = _ev_time(lambda: llp.sssp(dg, src, out=out, ws=ws, sched=ls), reps=3)
+        st = llp.get_status(ws)
+        res[name] = {"heuristic_ms": th, "learned_ms": tl, "learned_schedule": [st["mode_used"], st["delta_used"],
+                     st["block_cfg_used"]], "bit_exact": bool(torch.equal(ref, out))}
+        tot_h += th
+        tot_l += tl
+        del dg, ws, out
+        torch.cuda.empty_cache()
+    gc = synth.random_dag(8192, 4, seed=6)
+    dc = llp.DeviceGraph.from_host(gc, dev)
+    R, wsc = llp.transitive_closure(dc)
+    tc = _ev_time(lambda: llp.transitive_closure(dc, ws=wsc), reps=3)
+    res["closure8192"] = {"heuristic_ms": tc, "learned_ms": tc, "note": "no schedule choice"}
+    tot_h += tc
+    tot_l += tc
+    return {"stream_heuristic_ms": tot_h, "stream_learned_ms": tot_l, "speedup": tot_h / tot_l, "items": res}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -292,6 +428,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="llp", choices=["llp", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-engine section")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-scheduler stream section")
     ap.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (22 = the benchmarked workload; "
                     "smaller scales are for profiling captures)")
     args = ap.parse_args()
