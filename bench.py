@@ -30,6 +30,20 @@ sys.path.insert(0, ROOT)
 SCALE = 22
 WORKLOAD = "rmat22_ef16_sssp"
 
+# DRAM traffic of the sweep kernel per algorithmic byte, from one ncu capture at
+# R-MAT scale 20 (profiles/graph_sweep_sssp_rmat20_full.md), valid only for the
+# kernel source it was taken from (sha256 prefix of graph_sweep.cu + llp_common.cuh).
+TRAFFIC_CAPTURE = {"src_sha": "89915bab5f33df7f", "bytes_per_alg_byte": 1.2476}
+
+
+def kernel_src_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("graph_sweep.cu", "llp_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2603_13147_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
@@ -206,6 +220,9 @@ def run_gpu(args):
     alg_bytes = 8 * mr + 8 * g.n
     peak, peak_kind = peaks()
     achieved = alg_bytes / (ms * 1e-3) / 1e9
+    traffic = None
+    if kernel_src_sha() == TRAFFIC_CAPTURE["src_sha"]:
+        traffic = int(TRAFFIC_CAPTURE["bytes_per_alg_byte"] * alg_bytes)
 
     # BFS on the same graph (reported beside the headline)
     for _ in range(2):
@@ -259,7 +276,7 @@ def run_gpu(args):
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "schedule": {k: st[k] for k in ("mode_used", "delta_used", "block_cfg_used")}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind, "frac_of_nominal_8tbs": achieved / 8000.0,
+                     "traffic": traffic, "traffic_note": "scaled from an R-MAT scale 20 capture by algorithmic bytes", "peak_kind": peak_kind, "frac_of_nominal_8tbs": achieved / 8000.0,
                      "alg_bytes_per_launch": alg_bytes, "kernel": "graph_sweep_kernel<int32,false>"},
         "sweep_stats": {"sweeps": st["sweeps"], "edges_scanned": st["edges"], "advances": st["advances"],
                         "dense_sweeps": st["dense_sweeps"], "edges_per_reached_arc": st["edges"] / max(mr, 1),
