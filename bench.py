@@ -100,6 +100,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def combine_ranks(ms_local: float, units_local: int, device=None):
+    """Whole-job numbers over the process group: the max step time over ranks and the
+    units processed by all ranks (summed).  Single-process: the local values."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_local, units_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -207,13 +221,8 @@ def run_gpu(args):
     ms = float(np.mean(step_ms))
     st = llp.get_status(ws)
     slog = llp.sweep_log(ws)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-        dist.barrier()
-    value = world * mr / (ms * 1e-3) / 1e9
+    ms, units = combine_ranks(ms, mr, device=dev)
+    value = units / (ms * 1e-3) / 1e9
 
     # roofline of the sweep kernel: algorithmic bytes 8*m_r (index + weight per
     # arc of a reached vertex) + 8*n (offsets pair / distance per vertex)
