@@ -85,6 +85,11 @@ typedef struct llp_sched {
     int32_t threads;        /* threads per CTA: 0 = auto, else 256 or 512 */
     int64_t deadline_ns;    /* device wait limit of one call; 0 = default (10 s) */
     const float *mlp_params;/* device pointer to the scheduler network's parameters when use_mlp = 1 */
+    int32_t local_chain;    /* graph sweep: a warp expands the small vertices it has just advanced
+                               itself within the same sweep (LIFO, the paper's recency-biased per-thread
+                               bags), up to local_chain batches of 32 per worklist item;
+                               0 = heuristic (off), -1 = off */
+    int32_t reserved;
 } llp_sched_t;
 
 /* Work-block configurations of the graph sweep: (small-vertex degree limit,
@@ -105,6 +110,8 @@ typedef struct llp_stats {
     uint32_t delta_used;
     int32_t block_cfg_used;
     int32_t dense_sweeps; /* sweeps run in dense mode */
+    int32_t local_chain_used;
+    int32_t reserved;
 } llp_stats_t;
 
 const char *llp_version(void);
@@ -284,9 +291,10 @@ llp_status_t llp_batch_autotune(const llp_batch_t *b, void *ws, size_t ws_bytes,
  * of the graph sweep.  Setting llp_sched_t.use_mlp = 1 and mlp_params makes
  * llp_sssp / llp_bfs run a feature kernel and an inference kernel on the device
  * before the sweep, which then uses the chosen schedule.  Results never depend
- * on the schedule.  The scheduler network is features(16) -> 64 -> 64 -> 14
+ * on the schedule.  The scheduler network is features(16) -> 64 -> 64 -> 18
  * logits = heads {mode: 3 (AUTO, SPARSE, DENSE), bucket-width class: 8
- * (0 = none, c >= 1: width = max sampled weight * 2^(c-3)), block_cfg: 3}.
+ * (0 = none, c >= 1: width = max sampled weight * 2^(c-3)), block_cfg: 3,
+ * local chain: 4 (off, 4, 16, 64 batches)}.
  * Parameters: one fp32 vector, row-major W1[F,H1] b1 W2[H1,H2] b2 W3[H2,O] b3. */
 typedef struct llp_mlp_dims {
     int32_t F, H1, H2, O; /* each 1..128 */
@@ -313,7 +321,7 @@ llp_status_t llp_mlp_adam(float *params, const float *grad, float *m, float *v, 
                           float beta1, float beta2, float eps, void *stream);
 
 /* Runs only the feature and inference kernels for graph g (the default
- * 16-64-64-14 network) into the header of ws.  If h_chosen / h_features are not
+ * 16-64-64-18 network) into the header of ws.  If h_chosen / h_features are not
  * NULL, synchronises the stream and copies the choice / the 16 features out. */
 llp_status_t llp_graph_schedule(const llp_csr_t *g, int32_t source, int32_t unit_weights, const float *params,
                                 void *ws, size_t ws_bytes, void *stream, llp_sched_t *h_chosen, float *h_features);

@@ -42,14 +42,16 @@ class Csr(ctypes.Structure):
 class Sched(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("delta", ctypes.c_uint32), ("block_cfg", ctypes.c_int32),
                 ("dense_permille", ctypes.c_int32), ("use_mlp", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("deadline_ns", ctypes.c_int64), ("mlp_params", ctypes.c_void_p)]
+                ("deadline_ns", ctypes.c_int64), ("mlp_params", ctypes.c_void_p), ("local_chain", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("items", ctypes.c_int64),
                 ("edges", ctypes.c_int64), ("advances", ctypes.c_int64), ("aux", ctypes.c_int64),
                 ("elapsed_ns", ctypes.c_int64), ("mode_used", ctypes.c_int32), ("delta_used", ctypes.c_uint32),
-                ("block_cfg_used", ctypes.c_int32), ("dense_sweeps", ctypes.c_int32)]
+                ("block_cfg_used", ctypes.c_int32), ("dense_sweeps", ctypes.c_int32),
+                ("local_chain_used", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -85,8 +87,9 @@ def status_string(code: int) -> str:
 
 
 def make_sched(mode=0, delta=0, block_cfg=0, dense_permille=0, use_mlp=0, threads=0, deadline_ns=0,
-               mlp_params=None) -> Sched:
+               mlp_params=None, local_chain=0) -> Sched:
     s = Sched()
+    s.local_chain = local_chain
     s.mode, s.delta, s.block_cfg, s.dense_permille = mode, delta, block_cfg, dense_permille
     s.use_mlp, s.threads, s.deadline_ns = use_mlp, threads, deadline_ns
     s.mlp_params = None if mlp_params is None else mlp_params.data_ptr()
@@ -436,7 +439,7 @@ class MlpDims(ctypes.Structure):
 
 
 SCHED_F, SCHED_H1, SCHED_H2 = 16, 64, 64
-SCHED_HEADS = (3, 8, 3)  # mode, bucket-width class, block_cfg
+SCHED_HEADS = (3, 8, 3, 4)  # mode, bucket-width class, block_cfg, local-chain class
 
 
 def mlp_dims(F=SCHED_F, H1=SCHED_H1, H2=SCHED_H2, heads=SCHED_HEADS) -> MlpDims:

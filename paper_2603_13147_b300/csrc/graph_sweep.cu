@@ -84,6 +84,7 @@ struct GraphArgs {
     int32_t chunk_edges;
     int32_t cfg;
     int32_t use_dev_sched;  // 1: take mode/delta/cfg from the header (learned scheduler)
+    int32_t local_chain;    // batches per worklist item of the local chain, 0 = off
     long long deadline_ns;
 };
 
@@ -95,6 +96,12 @@ struct SweepCtx {
     unsigned long long bucket_hi;  // exclusive bound of the current bucket
     uint32_t fa;                   // far-list generation
     bool dense_next;               // small advances only set their bitmap bit
+    // local chaining (recency-biased per-warp bag): advanced small vertices are
+    // expanded by the same warp within the sweep, LIFO, from a shared-memory stack
+    int32_t *lq;
+    uint32_t lq_n = 0;
+    int32_t chain = 0;             // batches of 32 a warp may take from its stack per worklist item
+    bool chain_on = false;
     uint32_t *bm_cur, *bm_next;
     unsigned long long items = 0, edges = 0, adv = 0;
     uint32_t marked = 0;           // dense_next marks (an upper bound of the next frontier)
@@ -105,8 +112,9 @@ struct SweepCtx {
 };
 
 constexpr uint32_t kStageSmall = 128;  // entries per warp
-constexpr uint32_t kStageChunk = 256;
-constexpr uint32_t kDirectChunks = 8;  // a lane with more chunk entries reserves them directly
+constexpr uint32_t kStageChunk = 128;
+constexpr uint32_t kDirectChunks = 4;  // a lane with more chunk entries reserves them directly
+constexpr uint32_t kLocalQ = 128;      // per-warp stack of the local chain
 
 // Moves a warp's staged entries to the global list (one reservation).
 template <typename T>
@@ -136,8 +144,34 @@ __device__ __forceinline__ uint32_t key_dist(unsigned long long kv) { return (ui
 // Put the advanced vertices v[j] (want[j], class cls[j]) into the worklist of
 // sweep k+1, all kUnroll of them at once.  Warp-collective.
 template <typename OffT, int U>
-__device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, const bool (&want)[U], const int32_t (&v)[U],
+__device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, const bool (&want_in)[U], const int32_t (&v)[U],
                                           const uint32_t (&cls)[U], SweepCtx &c) {
+    bool want[U];
+#pragma unroll
+    for (int j = 0; j < U; j++) want[j] = want_in[j];
+    if (c.chain_on) {
+        // small advances stay with this warp when its stack has room for all of them
+        uint32_t nl = 0;
+#pragma unroll
+        for (int j = 0; j < U; j++) nl += (want[j] && cls[j] == 1);
+        uint32_t incl = nl;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane_id() >= o) incl += t;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (tot > 0 && c.lq_n + tot <= kLocalQ) {
+            uint32_t slot = c.lq_n + incl - nl;
+#pragma unroll
+            for (int j = 0; j < U; j++)
+                if (want[j] && cls[j] == 1) {
+                    c.lq[slot++] = v[j];
+                    want[j] = false;
+                }
+            c.lq_n += tot;
+        }
+    }
     bool newly[U];
     uint32_t n_small = 0, n_large = 0;
 #pragma unroll
@@ -322,6 +356,38 @@ __device__ __forceinline__ void expand_group(const GraphArgs<OffT> &a, bool vali
     }
 }
 
+// Local chain: the warp pops up to 32 vertices at a time from the top of its
+// stack (most recent first) and expands them, for at most c.chain batches;
+// whatever is left goes to the next sweep's worklist.  Warp-collective.
+template <typename OffT, bool UNIT>
+__device__ __forceinline__ void drain_local(const GraphArgs<OffT> &a, SweepCtx &c) {
+    int32_t budget = c.chain;
+    while (c.lq_n > 0 && budget > 0) {
+        __syncwarp();
+        const uint32_t cnt = c.lq_n < 32u ? c.lq_n : 32u;
+        const bool ok = lane_id() < cnt;
+        const int32_t u = ok ? c.lq[c.lq_n - cnt + lane_id()] : 0;
+        __syncwarp();
+        c.lq_n -= cnt;
+        budget--;
+        expand_group<OffT, UNIT>(a, ok, u, c);
+    }
+    if (c.lq_n > 0) {
+        c.chain_on = false;
+        while (c.lq_n > 0) {
+            __syncwarp();
+            const uint32_t cnt = c.lq_n < 32u ? c.lq_n : 32u;
+            const bool w1[1] = {lane_id() < cnt};
+            const int32_t u1[1] = {w1[0] ? c.lq[c.lq_n - cnt + lane_id()] : 0};
+            const uint32_t c1[1] = {w1[0] ? 1u : 0u};
+            __syncwarp();
+            c.lq_n -= cnt;
+            push_near(a, w1, u1, c1, c);
+        }
+        c.chain_on = true;
+    }
+}
+
 // One chunk (<= chunk_edges arcs) of one large vertex.
 template <typename OffT, bool UNIT>
 __device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item, SweepCtx &c) {
@@ -436,6 +502,7 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
     __shared__ uint32_t s_work[2];
     __shared__ int32_t s_stage_small[16][kStageSmall];
     __shared__ int2 s_stage_chunk[16][kStageChunk];
+    __shared__ int32_t s_lq[16][kLocalQ];
     WsHeader *h = a.h;
     const long long t0 = globaltimer_ns();
     const long long deadline = t0 + a.deadline_ns;
@@ -491,6 +558,7 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
         h->mode_used = c.mode;
         h->delta_used = c.delta;
         h->block_cfg_used = c.cfg;
+        h->scratch[8] = (uint32_t)c.chain;
         for (int i = 0; i < 3; i++) h->far_min[i] = kInf;
         h->list_ok[1] = 1;
     }
@@ -513,6 +581,9 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
 
     c.st_small = s_stage_small[threadIdx.x >> 5];
     c.st_chunk = s_stage_chunk[threadIdx.x >> 5];
+    c.lq = s_lq[threadIdx.x >> 5];
+    c.chain = a.local_chain;
+    if (a.use_dev_sched && *(volatile int32_t *)&h->sched_valid) c.chain = *(volatile int32_t *)&h->sched_chain;
     c.k = 1;
     c.fa = 0;
     c.bucket_hi = (c.delta == kInf) ? (1ull << 40) : (unsigned long long)c.delta;
@@ -585,7 +656,11 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
             dense_sweeps += dense;
             // chunks: static round robin (uniform cost, <= chunk_edges arcs)
             const int2 *cl = a.chunk[k & 1];
-            for (int64_t it = gwarp; it < nc; it += nwarps) expand_chunk<OffT, UNIT>(a, cl[it], c);
+            c.chain_on = c.chain > 0;
+            for (int64_t it = gwarp; it < nc; it += nwarps) {
+                expand_chunk<OffT, UNIT>(a, cl[it], c);
+                if (c.chain_on) drain_local<OffT, UNIT>(a, c);
+            }
             // vertex groups (their cost varies): CTA b owns groups b, b + G, b + 2G, ...
             // (G = grid size) and its warps take them in turn from a shared counter
             const uint32_t ngroups = dense ? (uint32_t)(((int64_t)a.nwords + kGroupWords - 1) / kGroupWords)
@@ -600,6 +675,7 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
                 const uint32_t g = (uint32_t)g64;
                 if (dense) {
                     scan_words<OffT, UNIT>(a, g, c);
+                    if (c.chain_on) drain_local<OffT, UNIT>(a, c);
                 } else {
                     const int64_t i = (int64_t)g * 32 + lane_id();
                     bool ok = i < ns;
@@ -610,8 +686,10 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
                         ok = (__ldcg(c.bm_next + (u >> 5)) & bit) == 0;
                     }
                     expand_group<OffT, UNIT>(a, ok, u, c);
+                    if (c.chain_on) drain_local<OffT, UNIT>(a, c);
                 }
             }
+            c.chain_on = false;
         }
         flush_sweep(a, c, &s_flush);
         alive = grid_barrier(h, phase, deadline);
@@ -741,6 +819,7 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         args.chunk_edges = bc.chunk;
         args.cfg = cfg;
         args.use_dev_sched = learned ? 1 : 0;
+        args.local_chain = (s && s->local_chain > 0) ? s->local_chain : 0;
         args.deadline_ns = deadline_from(s);
     };
     if (g->offsets_64) {

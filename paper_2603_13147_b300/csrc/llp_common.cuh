@@ -60,6 +60,7 @@ struct alignas(256) WsHeader {
     int32_t sched_mode;
     uint32_t sched_delta;
     int32_t sched_cfg;
+    int32_t sched_chain;
     int32_t sched_valid;
     float feat[16];  // instance features the choice was made from
     float feat_wmax; // largest sampled arc weight

@@ -61,40 +61,53 @@ def _time_call(fn, reps=3, cap_ms=None):
     return float(np.median(ts))
 
 
-def label_graph(dg: B.DeviceGraph, source: int, unit: bool, wmax: int, ws=None):
-    """Coordinate search over (bucket class, mode, block_cfg); returns (label triple, timing log)."""
+CHAIN_OF_CLASS = (0, 4, 16, 64)
+
+
+def label_graph(dg: B.DeviceGraph, source: int, unit: bool, wmax: int, ws=None, passes: int = 2,
+                margin: float = 0.03):
+    """Coordinate search over (mode, bucket class, block class, chain class), starting from the
+    heuristic default; a coordinate moves only when a candidate is faster by more than `margin`.
+    Returns (label tuple of class indices, timing log, best ms)."""
     if ws is None:
         ws = B.workspace(B.sssp_workspace_size(dg.n, dg.m), dg.indices.device)
     out = torch.empty(dg.n, dtype=torch.int32, device=dg.indices.device)
     fn = B.bfs if unit else B.sssp
     log = {}
 
-    def run(mode, dc, cfg, cap):
-        s = B.make_sched(mode=mode, delta=delta_of_class(dc, wmax), block_cfg=cfg)
+    def run(lab, cap):
+        key = ",".join(map(str, lab))
+        if key in log:
+            return log[key]
+        s = B.make_sched(mode=lab[0], delta=delta_of_class(lab[1], wmax), block_cfg=lab[2] + 1,
+                         local_chain=CHAIN_OF_CLASS[lab[3]] if lab[3] else -1)
         t = _time_call(lambda: fn(dg, source, out=out, sched=s, ws=ws), cap_ms=cap)
-        log[f"{mode},{dc},{cfg}"] = t
+        log[key] = t
         return t
 
-    best_t, best = float("inf"), (0, 0, 2)
-    classes = [0] if unit else list(range(N_DELTA_CLASSES))
-    for dc in classes:
-        t = run(0, dc, 2, 20 * best_t if best_t < float("inf") else None)
-        if t < best_t:
-            best_t, best = t, (0, dc, 2)
-    for mode in (1, 2):
-        t = run(mode, best[1], 2, 20 * best_t)
-        if t < best_t:
-            best_t, best = t, (mode, best[1], 2)
-    for cfg in (1, 3):
-        t = run(best[0], best[1], cfg, 20 * best_t)
-        if t < best_t:
-            best_t, best = t, (best[0], best[1], cfg)
-    return best, log, best_t
+    best = [0, 0, 1, 0]  # AUTO, no buckets, block cfg 2, no chain: the heuristic default
+    best_t = run(best, None)
+    axes = [(1, [0] if unit else list(range(N_DELTA_CLASSES))), (0, [0, 1, 2]), (3, [0, 1, 2, 3]), (2, [0, 1, 2])]
+    for _ in range(passes):
+        moved = False
+        for ax, vals in axes:
+            for val in vals:
+                if val == best[ax]:
+                    continue
+                cand = list(best)
+                cand[ax] = val
+                t = run(cand, 20 * best_t)
+                if t < best_t * (1.0 - margin):
+                    best_t, best, moved = t, cand, True
+        if not moved:
+            break
+    return tuple(best), log, best_t
 
 
 def label_to_sched(label, wmax: int) -> B.Sched:
-    """Class triple (mode, bucket class, block class 0..2) -> schedule."""
-    return B.make_sched(mode=int(label[0]), delta=delta_of_class(int(label[1]), wmax), block_cfg=int(label[2]) + 1)
+    """Class tuple (mode, bucket class, block class 0..2, chain class 0..3) -> schedule."""
+    return B.make_sched(mode=int(label[0]), delta=delta_of_class(int(label[1]), wmax), block_cfg=int(label[2]) + 1,
+                        local_chain=CHAIN_OF_CLASS[int(label[3])] if int(label[3]) else -1)
 
 
 def training_graphs(seed: int = 11, quick: bool = False):
@@ -135,7 +148,7 @@ def collect(items, device="cuda", verbose=True):
         t0 = time.time()
         label, log, best_ms = label_graph(dg, src, unit, wmax)
         X.append(feats)
-        Y.append([label[0], label[1], label[2] - 1])  # block_cfg 1..3 -> class 0..2
+        Y.append(list(label))
         meta.append({"name": name, "label": label, "best_ms": best_ms, "log": log, "wall_s": time.time() - t0})
         if verbose:
             print(json.dumps({"name": name, "label": label, "best_ms": round(best_ms, 4)}), flush=True)

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 F, H1, H2 = 16, 64, 64
-HEADS = [3, 8, 3]
+HEADS = [3, 8, 3, 4]
 O = sum(HEADS)
 
 
@@ -79,7 +79,8 @@ def test_training_reduces_loss(llp):
     from paper_2603_13147_b300 import sched
     rng = np.random.default_rng(5)
     X = rng.normal(0, 1, (64, F)).astype(np.float32)
-    Y = np.stack([(X[:, 0] > 0).astype(int), (X[:, 1] > 0).astype(int) * 3, (X[:, 2] > 0).astype(int)], 1)
+    Y = np.stack([(X[:, 0] > 0).astype(int), (X[:, 1] > 0).astype(int) * 3, (X[:, 2] > 0).astype(int),
+                  (X[:, 3] > 0).astype(int) * 2], 1)
     params, hist = sched.train(X, Y.astype(np.int32), steps=400, lr=1e-2)
     assert hist[-1][1] < 0.5 * hist[0][1]
     assert (sched.predict(params, X) == Y).mean() > 0.9
@@ -97,9 +98,11 @@ def test_device_inference_matches_oracle_network(llp):
         assert abs(feats[0] - np.log2(g["n"] + 1)) < 1e-4 and abs(feats[1] - np.log2(g["m"] + 1)) < 1e-4
         z, _ = omlp.forward(th.astype(np.float64), np.array([feats], np.float64), F, H1, H2, O)
         z = z[0]
-        pred = [int(np.argmax(z[0:3])), int(np.argmax(z[3:11])), int(np.argmax(z[11:14]))]
+        pred = [int(np.argmax(z[0:3])), int(np.argmax(z[3:11])), int(np.argmax(z[11:14])),
+                int(np.argmax(z[14:18]))]
         assert chosen.mode == pred[0]
         assert chosen.block_cfg == pred[2] + 1
+        assert chosen.local_chain == sched.CHAIN_OF_CLASS[pred[3]]
         want = sched.delta_of_class(pred[1], sched.sampled_wmax(g))
         assert chosen.delta == want
 
