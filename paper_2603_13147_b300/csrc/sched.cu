@@ -36,13 +36,21 @@ namespace {
 
 // ------------------------------------------------------------- features
 
+constexpr int kFeatBlocks = 64;
+constexpr int kFeatThreads = 256;
+constexpr int kFeatSamples = 16384;  // vertices and arcs sampled (evenly spaced)
+
+// Instance features from an evenly spaced sample of vertices (degree
+// histogram, mean and max degree) and arcs (weight range and spread).  Many
+// CTAs accumulate into the header; the last CTA to finish writes the features.
 template <typename OffT>
-__global__ void __launch_bounds__(1024) graph_features_kernel(int32_t n, int64_t m, const OffT *off,
-                                                              const uint32_t *w, int32_t source, WsHeader *h) {
+__global__ void __launch_bounds__(kFeatThreads) graph_features_kernel(int32_t n, int64_t m, const OffT *off,
+                                                                      const uint32_t *w, int32_t source, WsHeader *h) {
     __shared__ unsigned int s_hist[6];
     __shared__ unsigned long long s_deg;
     __shared__ unsigned int s_maxdeg, s_wmin, s_wmax;
     __shared__ float s_wsum, s_wsq;
+    __shared__ int s_last;
     if (threadIdx.x < 6) s_hist[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         s_deg = 0;
@@ -53,10 +61,12 @@ __global__ void __launch_bounds__(1024) graph_features_kernel(int32_t n, int64_t
         s_wsq = 0.f;
     }
     __syncthreads();
-    const int32_t S = n < 65536 ? n : 65536;
+    const int32_t S = n < kFeatSamples ? n : kFeatSamples;
+    const int64_t Sw = m < kFeatSamples ? m : kFeatSamples;
+    const int stride = gridDim.x * blockDim.x;
     unsigned long long dsum = 0;
     unsigned int dmax = 0;
-    for (int32_t i = threadIdx.x; i < S; i += blockDim.x) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < S; i += stride) {
         const int64_t v = (int64_t)i * n / S;
         const unsigned int d = (unsigned int)(off[v + 1] - off[v]);
         const int b = d == 0 ? 0 : d < 4 ? 1 : d < 16 ? 2 : d < 64 ? 3 : d < 256 ? 4 : 5;
@@ -64,12 +74,10 @@ __global__ void __launch_bounds__(1024) graph_features_kernel(int32_t n, int64_t
         dsum += d;
         dmax = max(dmax, d);
     }
-    const int64_t Sw = m < 65536 ? m : 65536;
     unsigned int wmn = 0xFFFFFFFFu, wmx = 0;
     float ws = 0.f, wq = 0.f;
-    for (int64_t i = threadIdx.x; i < Sw && w; i += blockDim.x) {
-        const int64_t e = i * m / Sw;
-        const unsigned int x = w[e];
+    for (int64_t i = blockIdx.x * blockDim.x + threadIdx.x; i < Sw && w; i += stride) {
+        const unsigned int x = w[i * m / Sw];
         wmn = min(wmn, x);
         wmx = max(wmx, x);
         ws += (float)x;
@@ -82,28 +90,47 @@ __global__ void __launch_bounds__(1024) graph_features_kernel(int32_t n, int64_t
     atomicAdd(&s_wsum, ws);
     atomicAdd(&s_wsq, wq);
     __syncthreads();
+    // header accumulators: scratch[9..14] (zeroed with the header)
+    uint32_t *acc = h->scratch + 9;
+    if (threadIdx.x < 6) atomicAdd(acc + threadIdx.x, s_hist[threadIdx.x]);
     if (threadIdx.x == 0) {
-        const float fs = (float)(S > 0 ? S : 1);
-        const unsigned int sdeg = (unsigned int)(off[source + 1] - off[source]);
-        float *f = h->feat;
-        f[0] = log2f((float)n + 1.f);
-        f[1] = log2f((float)m + 1.f);
-        f[2] = log2f((float)m / (float)n + 1.f);
-        for (int b = 0; b < 6; b++) f[3 + b] = (float)s_hist[b] / fs;
-        f[9] = log2f((float)max(s_maxdeg, sdeg) + 1.f);
-        const bool unit = (w == nullptr) || Sw == 0;
-        const float wmax = unit ? 1.f : (float)s_wmax;
-        const float wmin = unit ? 1.f : (float)s_wmin;
-        const float mean = unit ? 1.f : s_wsum / (float)Sw;
-        const float var = unit ? 0.f : fmaxf(s_wsq / (float)Sw - mean * mean, 0.f);
-        f[10] = log2f(wmax + 1.f);
-        f[11] = log2f(wmin + 1.f);
-        f[12] = sqrtf(var) / fmaxf(mean, 1e-6f);
-        f[13] = unit ? 1.f : 0.f;
-        f[14] = log2f((float)sdeg + 1.f) - f[2];
-        f[15] = 1.f;
-        h->feat_wmax = wmax;
+        atomicMax((unsigned int *)&h->feat[0], s_maxdeg);  // staged in feat[] bit patterns
+        atomicMax((unsigned int *)&h->feat[1], s_wmax);
+        atomicMax((unsigned int *)&h->feat[2], ~s_wmin);    // max of complements = min
+        atomicAdd(&h->feat[3], s_wsum);
+        atomicAdd(&h->feat[4], s_wsq);
+        __threadfence();
+        s_last = atomicAdd(&h->scratch[15], 1u) + 1u == gridDim.x;
     }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    const unsigned int maxdeg = *(volatile unsigned int *)&h->feat[0];
+    const unsigned int swmax = *(volatile unsigned int *)&h->feat[1];
+    const unsigned int swmin = ~*(volatile unsigned int *)&h->feat[2];
+    const float wsum = *(volatile float *)&h->feat[3], wsq = *(volatile float *)&h->feat[4];
+    unsigned int hist[6];
+    for (int b = 0; b < 6; b++) hist[b] = *(volatile uint32_t *)&acc[b];
+    const float fs = (float)(S > 0 ? S : 1);
+    const unsigned int sdeg = (unsigned int)(off[source + 1] - off[source]);
+    float *f = h->feat;
+    const bool unit = (w == nullptr) || Sw == 0;
+    const float wmax = unit ? 1.f : (float)swmax;
+    const float wmin = unit ? 1.f : (float)swmin;
+    const float mean = unit ? 1.f : wsum / (float)Sw;
+    const float var = unit ? 0.f : fmaxf(wsq / (float)Sw - mean * mean, 0.f);
+    f[0] = log2f((float)n + 1.f);
+    f[1] = log2f((float)m + 1.f);
+    f[2] = log2f((float)m / (float)n + 1.f);
+    for (int b = 0; b < 6; b++) f[3 + b] = (float)hist[b] / fs;
+    f[9] = log2f((float)max(maxdeg, sdeg) + 1.f);
+    f[10] = log2f(wmax + 1.f);
+    f[11] = log2f(wmin + 1.f);
+    f[12] = sqrtf(var) / fmaxf(mean, 1e-6f);
+    f[13] = unit ? 1.f : 0.f;
+    f[14] = log2f((float)sdeg + 1.f) - f[2];
+    f[15] = 1.f;
+    h->feat_wmax = wmax;
 }
 
 // ------------------------------------------------------------- inference
@@ -333,9 +360,11 @@ llp_status_t enqueue_learned_schedule(const llp_csr_t *g, int32_t source, bool u
     d.heads[3] = 4;
     const uint32_t *w = unit ? nullptr : g->weights;
     if (g->offsets_64)
-        graph_features_kernel<int64_t><<<1, 1024, 0, st>>>(g->n, g->m, (const int64_t *)g->offsets, w, source, h);
+        graph_features_kernel<int64_t><<<kFeatBlocks, kFeatThreads, 0, st>>>(g->n, g->m, (const int64_t *)g->offsets,
+                                                                              w, source, h);
     else
-        graph_features_kernel<int32_t><<<1, 1024, 0, st>>>(g->n, g->m, (const int32_t *)g->offsets, w, source, h);
+        graph_features_kernel<int32_t><<<kFeatBlocks, kFeatThreads, 0, st>>>(g->n, g->m, (const int32_t *)g->offsets,
+                                                                              w, source, h);
     mlp_schedule_kernel<<<1, block_for(d), 0, st>>>(params, d, h);
     LLP_CUDA_TRY(cudaGetLastError());
     return LLP_OK;

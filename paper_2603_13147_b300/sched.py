@@ -31,7 +31,7 @@ def sampled_wmax(g: dict) -> int:
     m = int(g["m"])
     if w is None or m == 0:
         return 1
-    S = min(m, 65536)
+    S = min(m, 16384)
     e = (np.arange(S, dtype=np.int64) * m) // S
     return int(w[e].max())
 
