@@ -80,7 +80,8 @@ typedef struct llp_sched {
     uint32_t delta;         /* SSSP/BFS priority-bucket width in distance units; 0 = auto,
                                LLP_DELTA_INF = no buckets */
     int32_t block_cfg;      /* work-block configuration 1..LLP_BLOCK_CFGS (see below); 0 = auto */
-    int32_t dense_permille; /* AUTO mode: dense sweep when worklist > n * dense_permille / 1000 (0 = 50) */
+    int32_t dense_permille; /* AUTO mode: the next sweep is dense when this one examines more than
+                               m * dense_permille / 1000 arcs (0 = 50) */
     int32_t use_mlp;        /* 1: the learned scheduler model chooses mode, delta and block_cfg */
     int32_t threads;        /* threads per CTA: 0 = auto, else 256 or 512 */
     int64_t deadline_ns;    /* device wait limit of one call; 0 = default (10 s) */
@@ -94,7 +95,7 @@ typedef struct llp_sched {
 
 /* Work-block configurations of the graph sweep: (small-vertex degree limit,
  * arcs per chunk of a large vertex), selected by block_cfg:
- *   1: (16, 128)   2: (32, 256)   3: (64, 512) */
+ *   1: (32, 256)   2: (64, 256)   3: (128, 512) */
 #define LLP_BLOCK_CFGS 3
 
 /* Device-side outcome and counters of the last call that used a workspace. */
@@ -124,7 +125,8 @@ llp_status_t llp_get_status(const void *ws, void *stream, llp_stats_t *out);
 /* Synchronises `stream`, then copies up to max_records per-sweep records of
  * the last graph-engine call (SSSP/BFS) that used `ws` into out, 4 uint32 per
  * record: device ns since the call started, small-vertex worklist size, chunk
- * worklist size, flags (bit 0 dense sweep, bit 1 bucket advance).  Returns the
+ * worklist size, flags (bit 0 dense sweep, bit 1 bucket advance, bits 2..31
+ * arcs examined by the sweep / 1024).  Returns the
  * number of records, or -LLP_ERR_* on error.  Diagnostics and the learned
  * scheduler's training data; not needed for results. */
 int32_t llp_sweep_log(const void *ws, void *stream, uint32_t *out, int32_t max_records);

@@ -50,8 +50,11 @@ struct BlockCfg {
     int small_max;
     int chunk;
 };
+// (small-vertex out-degree limit, arcs per chunk of a large vertex); vertices
+// just above the limit cost a whole warp each, so the default keeps degrees up
+// to 64 in the lane-balanced 32-vertex groups.
 __host__ __device__ inline BlockCfg block_cfg_of(int c) {
-    return c == 1 ? BlockCfg{16, 128} : (c == 3 ? BlockCfg{64, 512} : BlockCfg{32, 256});
+    return c == 1 ? BlockCfg{32, 256} : (c == 3 ? BlockCfg{128, 512} : BlockCfg{64, 256});
 }
 
 constexpr int kUnroll = 4;  // arcs per lane in flight
@@ -105,6 +108,7 @@ struct SweepCtx {
     uint32_t *bm_cur, *bm_next;
     unsigned long long items = 0, edges = 0, adv = 0;
     uint32_t marked = 0;           // dense_next marks (an upper bound of the next frontier)
+    unsigned long long edges_flushed = 0;
     // per-warp shared-memory staging of worklist appends (warp-uniform counts)
     int32_t *st_small;
     int2 *st_chunk;
@@ -428,10 +432,11 @@ __device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item
     }
 }
 
-// Dense sweep item: 32 bitmap words (1024 vertices), loaded with one
-// coalesced access; for every non-empty word, its small vertices whose bit is
-// set (and not set again for the next sweep) are expanded, one lane per
-// vertex.  The words are cleared.
+// Dense sweep item: kGroupWords bitmap words (32 vertices each), loaded with
+// one coalesced access.  The small vertices whose bit is set (and not set again
+// for the next sweep) are compacted across the words, 32 per expansion, so a
+// warp's lanes stay filled when few vertices of a word are active.  The words
+// are cleared.
 template <typename OffT, bool UNIT>
 __device__ __forceinline__ void scan_words(const GraphArgs<OffT> &a, int64_t g, SweepCtx &c) {
     const int64_t wi = g * kGroupWords + lane_id();
@@ -443,13 +448,30 @@ __device__ __forceinline__ void scan_words(const GraphArgs<OffT> &a, int64_t g, 
             act = b & ~__ldg(&a.cls[wi].y) & ~__ldcg(c.bm_next + wi);
         }
     }
-    uint32_t todo = __ballot_sync(0xffffffffu, act != 0);
-    while (todo) {
-        const int src = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const uint32_t word = __shfl_sync(0xffffffffu, act, src);
-        const bool ok = (word >> lane_id()) & 1u;
-        expand_group<OffT, UNIT>(a, ok, (int32_t)((g * kGroupWords + src) * 32 + lane_id()), c);
+    const uint32_t cnt = __popc(act);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < kGroupWords; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane_id() >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, kGroupWords - 1);
+    const uint32_t excl = incl - cnt;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t t = base + lane_id();
+        int pos = 0;
+#pragma unroll
+        for (int sh = kGroupWords / 2; sh > 0; sh >>= 1) {
+            const uint32_t probe = __shfl_sync(0xffffffffu, incl, pos + sh - 1);
+            if (probe <= t) pos += sh;
+        }
+        const bool ok = t < total;
+        const int owner = ok ? pos : 0;
+        const uint32_t ex = __shfl_sync(0xffffffffu, excl, owner);
+        const uint32_t word = __shfl_sync(0xffffffffu, act, owner);
+        int32_t u = 0;
+        if (ok) u = (int32_t)((g * kGroupWords + owner) * 32 + __fns(word, 0, (int)(t - ex) + 1));
+        expand_group<OffT, UNIT>(a, ok, u, c);
     }
 }
 
@@ -458,6 +480,7 @@ __device__ __forceinline__ void scan_words(const GraphArgs<OffT> &a, int64_t g, 
 struct BlockFlush {
     uint32_t ns[16], nc[16];
     uint32_t base_s, base_c, marked;
+    unsigned long long edges;
 };
 
 template <typename OffT>
@@ -466,10 +489,13 @@ __device__ __forceinline__ void flush_sweep(const GraphArgs<OffT> &a, SweepCtx &
     const uint32_t nk = c.k + 1, nx = nk % 3;
     const uint32_t m = warp_sum(c.marked);
     c.marked = 0;
+    const unsigned long long de = warp_sum(c.edges - c.edges_flushed);
+    c.edges_flushed = c.edges;
     if (lane_id() == 0) {
         bf->ns[wid] = c.st_ns;
         bf->nc[wid] = c.st_nc;
         if (m) atomicAdd(&bf->marked, m);
+        if (de) atomicAdd(&bf->edges, de);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -486,6 +512,8 @@ __device__ __forceinline__ void flush_sweep(const GraphArgs<OffT> &a, SweepCtx &
         bf->base_c = (tc ? atomicAdd(&a.h->n_chunk[nx], tc) : 0u);
         if (bf->marked) atomicAdd(&a.h->n_small[nx], bf->marked);
         bf->marked = 0;
+        if (bf->edges) atomicAdd(&a.h->sweep_edges[c.k & 1], bf->edges);
+        bf->edges = 0;
     }
     __syncthreads();
     int32_t *ls = a.small[nk & 1] + bf->base_s + bf->ns[wid];
@@ -514,6 +542,7 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
     const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
     if (threadIdx.x == 0) {
         s_flush.marked = 0;
+        s_flush.edges = 0;
         s_work[0] = 0;
         s_work[1] = 0;
     }
@@ -537,20 +566,29 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
     }
 
     // ---- init_global_state / initial_states_to_process (paper Sec. 3.3)
-    for (int64_t base = gwarp * 32; base < a.n; base += nwarps * 32) {
-        const int64_t v = base + lane_id();
-        uint32_t deg = 0;
-        if (v < a.n) {
-            deg = (uint32_t)(__ldg(a.off + v + 1) - __ldg(a.off + v));
-            const unsigned long long cl = deg == 0 ? 0ull : (deg <= (uint32_t)c.small_max ? 1ull : 2ull);
-            a.key[v] = ((v == a.source) ? 0ull : ((unsigned long long)kInf << 32)) | cl;
+    // four groups of 32 vertices per warp and iteration (loads in flight together)
+    for (int64_t base = gwarp * 128; base < a.n; base += nwarps * 128) {
+        uint32_t deg[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int64_t v = base + 32 * q + lane_id();
+            deg[q] = v < a.n ? (uint32_t)(__ldg(a.off + v + 1) - __ldg(a.off + v)) : 0u;
         }
-        const uint32_t has = __ballot_sync(0xffffffffu, deg > 0);
-        const uint32_t large = __ballot_sync(0xffffffffu, deg > (uint32_t)c.small_max);
-        if (lane_id() == 0) {
-            a.cls[base >> 5] = make_uint2(has, large);
-            a.bm[0][base >> 5] = 0u;
-            a.bm[1][base >> 5] = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int64_t v = base + 32 * q + lane_id();
+            if (v < a.n) {
+                const unsigned long long cl = deg[q] == 0 ? 0ull : (deg[q] <= (uint32_t)c.small_max ? 1ull : 2ull);
+                a.key[v] = ((v == a.source) ? 0ull : ((unsigned long long)kInf << 32)) | cl;
+            }
+            const uint32_t has = __ballot_sync(0xffffffffu, deg[q] > 0);
+            const uint32_t large = __ballot_sync(0xffffffffu, deg[q] > (uint32_t)c.small_max);
+            if (lane_id() == 0 && base + 32 * q < a.n) {
+                const int64_t wi = (base >> 5) + q;
+                a.cls[wi] = make_uint2(has, large);
+                a.bm[0][wi] = 0u;
+                a.bm[1][wi] = 0u;
+            }
         }
     }
     if (gtid == 0) {
@@ -610,6 +648,13 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
             if (k - 1 < kSweepLogCap)
                 sweep_log(h)[k - 1] = SweepRec{(uint32_t)(globaltimer_ns() - t0), ns, nc,
                                                (dense ? 1u : 0u) | (ns + nc == 0 ? 2u : 0u)};
+            // arcs examined by the previous sweep, in units of 1024 (bits 2..31 of its flags)
+            const unsigned long long pe = *(volatile unsigned long long *)&h->sweep_edges[(k - 1) & 1];
+            h->sweep_edges[(k - 1) & 1] = 0;
+            if (k >= 2 && k - 2 < kSweepLogCap) {
+                const unsigned long long q = min(pe >> 10, 0x3FFFFFFFull);
+                sweep_log(h)[k - 2].flags |= (uint32_t)(q << 2);
+            }
         }
         if (ns + nc == 0) {
             // near worklist empty: move to the next non-empty bucket, or stop
@@ -761,7 +806,7 @@ void resolve_schedule(const llp_sched_t *s, bool unit, int32_t n, int64_t m, int
     cfg = s ? s->block_cfg : 0;
     if (cfg < 1 || cfg > LLP_BLOCK_CFGS) cfg = 2;
     // dense sweeps once a sweep touches more than permille/1000 of the arcs
-    const int pm = (s && s->dense_permille > 0) ? s->dense_permille : 20;
+    const int pm = (s && s->dense_permille > 0) ? s->dense_permille : 50;
     dense_arcs = (unsigned long long)m * (unsigned long long)pm / 1000ull;
     (void)n;
     threads = (s && (s->threads == 256 || s->threads == 512)) ? s->threads : 512;

@@ -55,6 +55,7 @@ struct alignas(256) WsHeader {
     alignas(128) uint32_t n_far[3];
     uint32_t far_min[3];
     uint32_t list_ok[3];
+    unsigned long long sweep_edges[2];
     uint32_t scratch[16];
     // ---- schedule chosen on the device by the learned scheduler (graph engine)
     int32_t sched_mode;
