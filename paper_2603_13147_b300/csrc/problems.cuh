@@ -70,25 +70,40 @@ __device__ __forceinline__ unsigned long long propose_chain(int32_t m, int32_t k
 template <int R>
 __device__ __forceinline__ void knapsack_cta(int32_t n, const int32_t *w, const int32_t *v, int32_t W, int32_t *row,
                                              WsHeader *h) {
-    const int T = blockDim.x;
-    for (int32_t c = threadIdx.x; c <= W; c += T) row[c] = 0;
+    const int32_t T = blockDim.x;
+    const int32_t tid = threadIdx.x;
+    for (int32_t c = tid; c <= W; c += T) row[c] = 0;
     __syncthreads();
-    const int64_t chunk = (int64_t)T * R;
+    const int32_t chunk = T * R;  // capacities are < 2^26, so 32-bit indices suffice
     for (int32_t k = 0; k < n; k++) {
         const int32_t wk = __ldg(w + k);
         const int32_t vk = __ldg(v + k);
         if (wk > W) continue;  // item never fits: row unchanged (uniform branch)
         if (wk < 1 || vk < 0) {  // outside the problem statement: report, skip
-            if (threadIdx.x == 0 && h) set_status(h, LLP_ERR_INVALID_ARG);
+            if (tid == 0 && h) set_status(h, LLP_ERR_INVALID_ARG);
             continue;
         }
-        // chunks from the top; the lowest chunk may be partial
-        for (int64_t top = (int64_t)W + 1; top > wk; top -= chunk) {
-            const int64_t lo = top - chunk > wk ? top - chunk : (int64_t)wk;
+        // full chunks from the top, then the partial lowest chunk [wk, top)
+        int32_t top = W + 1;
+        for (; top - chunk >= wk; top -= chunk) {
+            const int32_t *src = row + (top - chunk) + tid;
             int32_t nv[R];
 #pragma unroll
             for (int r = 0; r < R; r++) {
-                const int64_t c = lo + (int64_t)r * T + threadIdx.x;
+                const int32_t keep = src[r * T];
+                const int32_t take = src[r * T - wk] + vk;
+                nv[r] = keep > take ? keep : take;
+            }
+            __syncthreads();
+            int32_t *dst = row + (top - chunk) + tid;
+#pragma unroll
+            for (int r = 0; r < R; r++) dst[r * T] = nv[r];
+        }
+        if (top > wk) {
+            int32_t nv[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int32_t c = wk + r * T + tid;
                 nv[r] = 0;
                 if (c < top) {
                     const int32_t keep = row[c];
@@ -99,7 +114,7 @@ __device__ __forceinline__ void knapsack_cta(int32_t n, const int32_t *w, const 
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < R; r++) {
-                const int64_t c = lo + (int64_t)r * T + threadIdx.x;
+                const int32_t c = wk + r * T + tid;
                 if (c < top) row[c] = nv[r];
             }
         }
