@@ -299,6 +299,8 @@ def run_gpu(args):
         "clocks": clocks.summary(),
         "wall_s_timed": t_wall,
     }
+    if not args.no_functors:
+        line["functors"] = bench_functors(llp, dev)
     if not args.no_batched:
         line["batched"] = bench_batched(llp, dev, stream)
     if not args.no_learned:
@@ -404,6 +406,66 @@ def bench_batched(llp, dev, stream):
             "status": bst["status"], "cuda_graph": True}
 
 
+def bench_functors(llp, dev):
+    """Every other problem of the sweep on its configured workload, device time (CUDA events)."""
+    import torch
+    import synth
+    out = {}
+    # config 1: ER 16,384 / 131,072, source 0 (latency-bound: the input lives in L2)
+    g = synth.er16k()
+    dg = llp.DeviceGraph.from_host(g, dev)
+    ws = llp.workspace(llp.sssp_workspace_size(g["n"], g["m"]), dev)
+    d = torch.empty(g["n"], dtype=torch.int32, device=dev)
+    t = _ev_time(lambda: llp.sssp(dg, 0, out=d, ws=ws), reps=5)
+    st = llp.get_status(ws)
+    tb = _ev_time(lambda: llp.bfs(dg, 0, out=d, ws=ws), reps=5)
+    out["er16k_sssp"] = {"ms": t, "sweeps": st["sweeps"], "gteps": g["m"] / (t * 1e-3) / 1e9}
+    out["er16k_bfs"] = {"ms": tb, "gteps": g["m"] / (tb * 1e-3) / 1e9}
+    # config 3: stable marriage, n = 16,384 random and n = 8,192 with one shared men's order
+    for name, n, adv, seed in (("marriage16384_random", 16384, False, 3), ("marriage8192_shared", 8192, True, 4)):
+        mp, wr = synth.marriage(n, seed=seed, adversarial=adv)
+        tmp, twr = torch.from_numpy(mp).to(dev), torch.from_numpy(wr).to(dev)
+        del mp, wr
+        wife, _, _, wsm = llp.stable_marriage(tmp, twr)
+        t = _ev_time(lambda: llp.stable_marriage(tmp, twr, ws=wsm, want_husband=False, want_next=False), reps=3)
+        st = llp.get_status(wsm)
+        out[name] = {"ms": t, "proposals": st["aux"], "proposals_per_s": st["aux"] / (t * 1e-3),
+                     "status": st["status"]}
+        del tmp, twr
+        torch.cuda.empty_cache()
+    # 0-1 knapsack, one instance n = 2,048, capacity 65,536 (one CTA)
+    w, v = synth.knapsack(2048, 65536, seed=5, stream=77)
+    tw, tv = torch.from_numpy(w).to(dev), torch.from_numpy(v).to(dev)
+    _, _, wsk = llp.knapsack(tw, tv, 65536, want_row=False)
+    t = _ev_time(lambda: llp.knapsack(tw, tv, 65536, want_row=False, ws=wsk), reps=3)
+    out["knapsack_2048x65536"] = {"ms": t, "cells_per_s": 2048 * 65537 / (t * 1e-3)}
+    # job scheduling, one DAG of 1,048,576 jobs (Poisson(3) forward arcs)
+    gj, dur = synth.job_dag(1 << 20, seed=5)
+    dgj = llp.DeviceGraph.from_host(gj, dev)
+    td = torch.from_numpy(dur).to(dev)
+    _, wsj = llp.job_schedule(dgj, td)
+    t = _ev_time(lambda: llp.job_schedule(dgj, td, ws=wsj), reps=3)
+    st = llp.get_status(wsj)
+    out["job_1M"] = {"ms": t, "jobs": gj["n"], "arcs": gj["m"], "sweeps": st["sweeps"], "status": st["status"]}
+    # transitive closure of a random DAG, n = 8,192, p = 4/n
+    gc = synth.random_dag(8192, 4, seed=6)
+    dc = llp.DeviceGraph.from_host(gc, dev)
+    _, wsc = llp.transitive_closure(dc)
+    t = _ev_time(lambda: llp.transitive_closure(dc, ws=wsc), reps=3)
+    st = llp.get_status(wsc)
+    out["closure_dag8192"] = {"ms": t, "sweeps": st["sweeps"], "pairs": st["advances"], "status": st["status"]}
+    # reduction of 2^28 uint64 (2 GiB, HBM-bound): roofline against the measured copy bandwidth
+    x = torch.randint(-(1 << 62), 1 << 62, (1 << 28,), dtype=torch.int64, device=dev)
+    _, wsr = llp.reduce_sum(x)
+    t = _ev_time(lambda: llp.reduce_sum(x, ws=wsr), reps=3)
+    peak, kind = peaks()
+    gbs = (8 << 28) / (t * 1e-3) / 1e9
+    out["reduce_2^28_u64"] = {"ms": t, "GB_per_s": gbs, "frac_of_measured_hbm": gbs / peak}
+    del x
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_learned(llp, dev, g22, s22):
     """Mixed stream: R-MAT scale 20/22/24 SSSP, 2048x2048 grid SSSP, closure of a random
     DAG (n=8192, p=4/n).  Learned schedule (network on the device) against the fixed
@@ -455,6 +517,7 @@ def main():
     ap.add_argument("--impl", default="llp", choices=["llp", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-engine section")
+    ap.add_argument("--no-functors", action="store_true", help="skip the other-problems section")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-scheduler stream section")
     ap.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (22 = the benchmarked workload; "
                     "smaller scales are for profiling captures)")
