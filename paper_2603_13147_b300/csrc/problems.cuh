@@ -23,32 +23,56 @@ __device__ __forceinline__ unsigned long long propose_chain(int32_t m, int32_t k
                                                             const int32_t *women_rank,
                                                             unsigned long long *best, int32_t *next,
                                                             WsHeader *h, long long deadline, bool &failed) {
-    unsigned long long proposals = 0;
+    constexpr int L = 8;  // look-ahead: the next L women of m are checked with independent loads
+    unsigned long long proposals = 0, rounds = 0;
     for (;;) {
         if (k >= n) {  // list exhausted: Algorithm LLP's "null" (advance beyond T[m])
             set_status(h, LLP_ERR_INFEASIBLE);
             failed = true;
             return proposals;
         }
-        if ((proposals & 1023ull) == 1023ull && globaltimer_ns() > deadline) {
+        if ((++rounds & 255ull) == 0 && globaltimer_ns() > deadline) {
             set_status(h, LLP_ERR_TIMEOUT);
             failed = true;
             return proposals;
         }
-        const int32_t w = __ldg(men_pref + (int64_t)m * n + k);
-        const uint32_t r = (uint32_t)__ldg(women_rank + (int64_t)w * n + m);
-        const unsigned long long mine = ((unsigned long long)r << 32) | (uint32_t)m;
-        proposals++;
-        // forbidden check without an atomic: w already holds a better suitor
-        const unsigned long long cur = *(volatile unsigned long long *)(best + w);
-        if (cur < mine) {
-            k++;
+        const int32_t cnt = (n - k) < L ? (n - k) : L;
+        const int32_t *pr = men_pref + (int64_t)m * n + k;
+        int32_t w[L];
+        unsigned long long mine[L], cur[L];
+#pragma unroll
+        for (int i = 0; i < L; i++) w[i] = i < cnt ? __ldg(pr + i) : 0;
+#pragma unroll
+        for (int i = 0; i < L; i++)
+            mine[i] = i < cnt ? (((unsigned long long)(uint32_t)__ldg(women_rank + (int64_t)w[i] * n + m) << 32) |
+                                 (uint32_t)m)
+                              : 0ull;
+#pragma unroll
+        for (int i = 0; i < L; i++) cur[i] = i < cnt ? *(volatile unsigned long long *)(best + w[i]) : 0ull;
+        // forbidden at w[i] (w already holds a better suitor) for every i before the first candidate
+        int cand = -1;
+#pragma unroll
+        for (int i = L - 1; i >= 0; i--)
+            if (i < cnt && cur[i] > mine[i]) cand = i;
+        if (cand < 0) {
+            proposals += cnt;
+            k += cnt;
             continue;
         }
+        proposals += cand + 1;
+        k += cand;
+        unsigned long long my = 0;
+        int32_t ww = 0;
+#pragma unroll
+        for (int i = 0; i < L; i++)
+            if (i == cand) {
+                my = mine[i];
+                ww = w[i];
+            }
         next[m] = k;
         __threadfence();
-        const unsigned long long old = atomicMin(best + w, mine);
-        if (old < mine) {  // lost the race: forbidden after all
+        const unsigned long long old = atomicMin(best + ww, my);
+        if (old < my) {  // lost the race: forbidden after all
             k++;
             continue;
         }
