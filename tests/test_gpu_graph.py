@@ -52,7 +52,9 @@ def csr_from_arcs(n, arcs):
 
 
 SCHEDS = [dict(), dict(mode=1), dict(mode=2), dict(mode=1, delta=64), dict(mode=0, delta=8, block_cfg=1),
-          dict(mode=2, delta=300, block_cfg=3, threads=256), dict(delta=1, block_cfg=1)]
+          dict(mode=2, delta=300, block_cfg=3, threads=256), dict(delta=1, block_cfg=1),
+          dict(mode=1, local_chain=4), dict(mode=2, local_chain=16, delta=500), dict(local_chain=64, block_cfg=3),
+          dict(mode=1, local_chain=1, delta=1, threads=256)]
 
 
 def test_paper_example(llp):
@@ -73,7 +75,7 @@ def test_sssp_er16k_all_schedules(llp, kw):
     assert st["advances"] >= int((ref != oracle.INF).sum()) - 1
 
 
-@pytest.mark.parametrize("kw", SCHEDS[:4])
+@pytest.mark.parametrize("kw", SCHEDS[:4] + SCHEDS[7:9])
 def test_bfs_er16k(llp, kw):
     g = synth.er16k()
     ref = oracle.bfs(g["offsets"], g["indices"], 0)
@@ -109,6 +111,29 @@ def test_random_small_and_ragged(llp, seed):
     refb = oracle.bfs(g["offsets"], g["indices"], s)
     d, _ = run_bfs(llp, g, s)
     assert (d == refb).all()
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(mode=1, local_chain=16), dict(mode=2, local_chain=4, delta=2000)])
+def test_grid_graph_schedules(llp, kw):
+    """Road-like input (2-D grid, both arc directions): long paths, thousands of sweeps."""
+    g = synth.grid_graph(96, 77, 1, 1000, seed=5)
+    ref = oracle.sssp(g["offsets"], g["indices"], g["weights"], 5)
+    d, _ = run_sssp(llp, g, 5, **kw)
+    assert (d == ref).all()
+    lv, _ = run_bfs(llp, g, 5, **kw)
+    assert (lv == oracle.bfs(g["offsets"], g["indices"], 5)).all()
+
+
+@pytest.mark.parametrize("n", [31, 33, 1023, 1025])
+def test_ragged_vertex_counts(llp, n):
+    """n not a multiple of the 32-vertex bitmap word; source = last vertex."""
+    rng = np.random.default_rng(n)
+    arcs = [(int(rng.integers(n)), int(rng.integers(n)), int(rng.integers(1, 20))) for _ in range(4 * n)]
+    arcs += [(n - 1, int(rng.integers(n)), 1) for _ in range(70)]  # a large source vertex
+    g = csr_from_arcs(n, arcs)
+    for kw in (dict(), dict(mode=2), dict(mode=1, local_chain=4)):
+        d, _ = run_sssp(llp, g, n - 1, **kw)
+        assert (d == oracle.sssp(g["offsets"], g["indices"], g["weights"], n - 1)).all()
 
 
 def test_edge_cases(llp):

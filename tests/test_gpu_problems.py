@@ -118,6 +118,13 @@ def test_job_random(llp, n, seed):
     assert (c.cpu().numpy() == oracle.job_schedule(dur, g["offsets"], g["indices"])).all()
 
 
+def test_job_int64_offsets(llp):
+    g, dur = synth.job_dag(20000, seed=9)
+    c, ws = llp.job_schedule(llp.DeviceGraph.from_host(g, "cuda", offsets_64=True), T(dur))
+    assert llp.get_status(ws)["status"] == 0
+    assert (c.cpu().numpy() == oracle.job_schedule(dur, g["offsets"], g["indices"])).all()
+
+
 def test_job_cycle_is_infeasible(llp):
     g = dict(n=3, m=3, offsets=np.array([0, 1, 2, 3], np.int64), indices=np.array([1, 2, 0], np.int32), weights=None)
     _, ws = llp.job_schedule(job_dev(llp, g), T(np.ones(3, np.int32)))
@@ -139,6 +146,16 @@ def test_closure_random_with_cycles(llp, n, seed):
     R, ws = llp.transitive_closure(llp.DeviceGraph.from_host(g, "cuda"))
     assert llp.get_status(ws)["status"] == 0
     assert (R.cpu().numpy().view(np.uint32) == oracle.transitive_closure(g["offsets"], g["indices"])).all()
+
+
+def test_closure_int64_offsets_and_chain(llp):
+    n = 300
+    g = dict(n=n, m=n - 1, offsets=np.concatenate([np.arange(n, dtype=np.int64), [n - 1]]),
+             indices=np.arange(1, n, dtype=np.int32), weights=None)
+    R, ws = llp.transitive_closure(llp.DeviceGraph.from_host(g, "cuda", offsets_64=True))
+    assert llp.get_status(ws)["status"] == 0
+    bits = np.unpackbits(R.cpu().numpy().view(np.uint8), axis=1, bitorder="little")[:, :n].astype(bool)
+    assert (bits == np.triu(np.ones((n, n), bool), 1)).all()  # closure of a chain
 
 
 def test_closure_random_dag_8192(llp):
