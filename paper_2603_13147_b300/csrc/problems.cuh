@@ -91,6 +91,47 @@ __device__ __forceinline__ unsigned long long propose_chain(int32_t m, int32_t k
 // max(G[k-1,c], v_k + G[k-1,c-w_k]) into registers, the CTA synchronises, then
 // writes; cells below the chunk are still G[k-1, *] when read, so one buffer
 // suffices.  Items with w < 1 or v < 0 set LLP_ERR_INVALID_ARG in h.
+// One item over capacities [wk, top), top-down chunks, in place.
+template <int R>
+__device__ __forceinline__ void knapsack_item(int32_t wk, int32_t vk, int32_t top, int32_t *row) {
+    const int32_t T = blockDim.x;
+    const int32_t tid = threadIdx.x;
+    const int32_t chunk = T * R;
+    for (; top - chunk >= wk; top -= chunk) {
+        const int32_t *src = row + (top - chunk) + tid;
+        int32_t nv[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int32_t keep = src[r * T];
+            const int32_t take = src[r * T - wk] + vk;
+            nv[r] = keep > take ? keep : take;
+        }
+        __syncthreads();
+        int32_t *dst = row + (top - chunk) + tid;
+#pragma unroll
+        for (int r = 0; r < R; r++) dst[r * T] = nv[r];
+    }
+    if (top > wk) {
+        int32_t nv[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int32_t c = wk + r * T + tid;
+            nv[r] = 0;
+            if (c < top) {
+                const int32_t keep = row[c];
+                const int32_t take = row[c - wk] + vk;
+                nv[r] = keep > take ? keep : take;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int32_t c = wk + r * T + tid;
+            if (c < top) row[c] = nv[r];
+        }
+    }
+}
+
 template <int R>
 __device__ __forceinline__ void knapsack_cta(int32_t n, const int32_t *w, const int32_t *v, int32_t W, int32_t *row,
                                              WsHeader *h) {
@@ -99,50 +140,56 @@ __device__ __forceinline__ void knapsack_cta(int32_t n, const int32_t *w, const 
     for (int32_t c = tid; c <= W; c += T) row[c] = 0;
     __syncthreads();
     const int32_t chunk = T * R;  // capacities are < 2^26, so 32-bit indices suffice
-    for (int32_t k = 0; k < n; k++) {
-        const int32_t wk = __ldg(w + k);
-        const int32_t vk = __ldg(v + k);
-        if (wk > W) continue;  // item never fits: row unchanged (uniform branch)
-        if (wk < 1 || vk < 0) {  // outside the problem statement: report, skip
+    int32_t k = 0;
+    while (k < n) {
+        const int32_t wa = __ldg(w + k), va = __ldg(v + k);
+        if (wa < 1 || va < 0) {  // outside the problem statement: report, skip
             if (tid == 0 && h) set_status(h, LLP_ERR_INVALID_ARG);
+            k++;
             continue;
         }
-        // full chunks from the top, then the partial lowest chunk [wk, top)
-        int32_t top = W + 1;
-        for (; top - chunk >= wk; top -= chunk) {
-            const int32_t *src = row + (top - chunk) + tid;
-            int32_t nv[R];
+        const int32_t wb = k + 1 < n ? __ldg(w + k + 1) : 0, vb = k + 1 < n ? __ldg(v + k + 1) : 0;
+        if (k + 1 < n && wb >= 1 && vb >= 0 && (int64_t)wa + wb <= W) {
+            // Two items (a, b) per pass for the capacities c >= w_a + w_b: the new
+            // row is max(n1[c], n1[c - w_b] + v_b) with n1[x] = max(o[x], o[x - w_a] + v_a),
+            // which reads the previous row o at c, c - w_a, c - w_b, c - w_a - w_b,
+            // all at or below c, so the top-down in-place chunking stays valid.
+            // 4 loads + 1 store per two cell updates instead of 6 + 2, half the barriers.
+            const int32_t wab = wa + wb;
+            int32_t top = W + 1;
+            for (; top - chunk >= wab; top -= chunk) {
+                const int32_t *src = row + (top - chunk) + tid;
+                int32_t nv[R];
 #pragma unroll
-            for (int r = 0; r < R; r++) {
-                const int32_t keep = src[r * T];
-                const int32_t take = src[r * T - wk] + vk;
-                nv[r] = keep > take ? keep : take;
-            }
-            __syncthreads();
-            int32_t *dst = row + (top - chunk) + tid;
-#pragma unroll
-            for (int r = 0; r < R; r++) dst[r * T] = nv[r];
-        }
-        if (top > wk) {
-            int32_t nv[R];
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-                const int32_t c = wk + r * T + tid;
-                nv[r] = 0;
-                if (c < top) {
-                    const int32_t keep = row[c];
-                    const int32_t take = row[c - wk] + vk;
-                    nv[r] = keep > take ? keep : take;
+                for (int r = 0; r < R; r++) {
+                    const int32_t oc = src[r * T];
+                    const int32_t oa = src[r * T - wa];
+                    const int32_t ob = src[r * T - wb];
+                    const int32_t oab = src[r * T - wab];
+                    const int32_t n1c = oc > oa + va ? oc : oa + va;
+                    const int32_t n1b = ob > oab + va ? ob : oab + va;
+                    nv[r] = n1c > n1b + vb ? n1c : n1b + vb;
                 }
+                __syncthreads();
+                int32_t *dst = row + (top - chunk) + tid;
+#pragma unroll
+                for (int r = 0; r < R; r++) dst[r * T] = nv[r];
             }
             __syncthreads();
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-                const int32_t c = wk + r * T + tid;
-                if (c < top) row[c] = nv[r];
-            }
+            // the capacities below: item a then item b, one at a time
+            const int32_t lo_top = top;  // cells [lo_top, W] hold both items already
+            knapsack_item<R>(wa, va, lo_top, row);
+            __syncthreads();
+            // item b over [wb, lo_top): cells in [lo_top, lo_top + wb) read only below lo_top... but
+            // cells >= lo_top are final, so b must only touch [wb, lo_top)
+            knapsack_item<R>(wb, vb, lo_top, row);
+            __syncthreads();
+            k += 2;
+            continue;
         }
+        if (wa <= W) knapsack_item<R>(wa, va, W + 1, row);
         __syncthreads();
+        k++;
     }
 }
 
