@@ -246,7 +246,30 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     bfs_ms = float(np.mean([a.elapsed_time(b) for a, b in bev]))
     bfs_st = llp.get_status(ws)
-    bfs_mr, _ = reached_arcs(g, llp.as_u32(dist_t))
+    bfs_lv = llp.as_u32(dist_t)
+    bfs_mr, _ = reached_arcs(g, bfs_lv)
+
+    # BFS with pull sweeps over the device transpose (built once, outside the timed steps)
+    torch.cuda.synchronize(dev)
+    tt0 = torch.cuda.Event(enable_timing=True); tt1 = torch.cuda.Event(enable_timing=True)
+    tt0.record(stream)
+    dg_in = dg.transpose()
+    tt1.record(stream)
+    for _ in range(2):
+        llp.bfs_pull(dg, dg_in, s, out=dist_t, ws=ws)
+    torch.cuda.synchronize(dev)
+    transpose_ms = tt0.elapsed_time(tt1)
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        pev[i][0].record(stream)
+        llp.bfs_pull(dg, dg_in, s, out=dist_t, ws=ws)
+        pev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    pull_ms = float(np.mean([a.elapsed_time(b) for a, b in pev]))
+    pull_st = llp.get_status(ws)
+    pull_same = bool((llp.as_u32(dist_t) == bfs_lv).all())
+    del dg_in
 
     # end to end through the public API from pinned host buffers
     import numpy as _np
@@ -292,7 +315,13 @@ def run_gpu(args):
                         "device_loop_ms": st["elapsed_ns"] / 1e6,
                         "per_sweep": [[round(int(r[0]) / 1e6, 4), int(r[1]), int(r[2]), int(r[3])] for r in slog]},
         "bfs": {"gteps": bfs_mr / (bfs_ms * 1e-3) / 1e9, "ms": bfs_ms, "sweeps": bfs_st["sweeps"],
-                "status": bfs_st["status"]},
+                "edges_scanned": bfs_st["edges"], "status": bfs_st["status"],
+                "pull": {"gteps": bfs_mr / (pull_ms * 1e-3) / 1e9, "ms": pull_ms, "sweeps": pull_st["sweeps"],
+                         "pull_sweeps": pull_st["pull_sweeps"], "edges_scanned": pull_st["edges"],
+                         "status": pull_st["status"], "levels_equal_push": pull_same,
+                         "transpose_ms": transpose_ms,
+                         "note": "llp_bfs_pull with the device transpose (built once, untimed); "
+                                 "GTEPS counts the reached arcs, as for push"}},
         "e2e": {"value": mr / (e2e_ms * 1e-3) / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": args.steps,

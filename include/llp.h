@@ -90,7 +90,9 @@ typedef struct llp_sched {
                                itself within the same sweep (LIFO, the paper's recency-biased per-thread
                                bags), up to local_chain batches of 32 per worklist item;
                                0 = heuristic (off), -1 = off */
-    int32_t reserved;
+    int32_t pull_permille;  /* llp_bfs_pull: a sweep runs pull-style over the in-arcs when its frontier
+                               holds more than about m * pull_permille / 1000 out-arcs (0 = 200);
+                               < 0 = never pull */
 } llp_sched_t;
 
 /* Work-block configurations of the graph sweep: (small-vertex degree limit,
@@ -112,7 +114,7 @@ typedef struct llp_stats {
     int32_t block_cfg_used;
     int32_t dense_sweeps; /* sweeps run in dense mode */
     int32_t local_chain_used;
-    int32_t reserved;
+    int32_t pull_sweeps;  /* llp_bfs_pull: sweeps run pull-style over the in-arcs */
 } llp_stats_t;
 
 const char *llp_version(void);
@@ -175,6 +177,35 @@ llp_status_t llp_sssp_noalloc(const llp_csr_t *g, int32_t source, uint32_t *dist
 size_t llp_bfs_workspace_size(int32_t n, int64_t m);
 llp_status_t llp_bfs(const llp_csr_t *g, int32_t source, uint32_t *level, const llp_sched_t *sched,
                      void *ws, size_t ws_bytes, void *stream);
+
+/* BFS with direction switching.  Same result as llp_bfs; g_in is the
+ * transpose of g (CSR of IN-arcs: row v lists the sources u of the arcs (u,v),
+ * any order within a row; same n, m and offsets_64 as g; weights ignored),
+ * e.g. built by llp_csr_transpose.  A sweep whose frontier is narrow runs
+ * push-style as in llp_bfs.  A sweep whose frontier is wide (see
+ * llp_sched_t.pull_permille) evaluates the predicate of Sec. 4.2 in its own
+ * direction, over in-neighbours: every vertex not yet reached scans its
+ * in-arcs and stops at the first one whose source is in the frontier, which
+ * gives it the next level.  The paper states the predicate this way; switching
+ * by frontier width is the hybrid its Conclusion (Future work) proposes for
+ * dense frontiers.  Pull sweeps are used only when the run keeps exact
+ * levels per sweep, i.e. without a local chain (llp_sched_t.local_chain);
+ * with a chain every sweep is push-style.  Workspace: llp_bfs_workspace_size. */
+llp_status_t llp_bfs_pull(const llp_csr_t *g, const llp_csr_t *g_in, int32_t source, uint32_t *level,
+                          const llp_sched_t *sched, void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------ Transpose
+ * Input preparation for llp_bfs_pull (not a step of the method): writes the
+ * transpose of g.  in_offsets: n+1 entries of g's offset type (int32 if
+ * g->offsets_64 == 0, else int64); in_indices[m]: row v holds the sources u of
+ * the arcs (u,v); in_weights[m] (may be NULL; needs g->weights) the matching
+ * weights.  The order of the arcs within a row is unspecified (it depends on
+ * timing); the rows as multisets and in_offsets are exact.  An arc whose
+ * target is outside [0, n) is skipped and sets LLP_ERR_INVALID_ARG as the
+ * device status. */
+size_t llp_csr_transpose_workspace_size(int32_t n, int64_t m);
+llp_status_t llp_csr_transpose(const llp_csr_t *g, void *in_offsets, int32_t *in_indices, uint32_t *in_weights,
+                               void *ws, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------- Stable marriage
  * Paper Sec. 4.3: G[m] = index into man m's preference list; m is forbidden

@@ -87,6 +87,21 @@ def bfs(offsets, indices, source: int) -> np.ndarray:
     return lv
 
 
+def csr_transpose(offsets, indices, weights=None):
+    """In-arc CSR by a stable counting sort on the target.  Returns (in_offsets int64, in_indices
+    int32, in_weights uint32 or None); row v lists the sources of the arcs into v in arc order."""
+    off = _c(offsets, np.int64); idx = _c(indices, np.int32)
+    n = off.shape[0] - 1
+    w = None if weights is None else _c(weights, np.uint32)
+    ioff = np.empty(n + 1, np.int64)
+    iidx = np.empty(idx.shape[0], np.int32)
+    iw = None if w is None else np.empty(idx.shape[0], np.uint32)
+    rc = _L().oracle_csr_transpose(ctypes.c_int32(n), _p(off), _p(idx), _p(w), _p(ioff), _p(iidx), _p(iw))
+    if rc:
+        raise OracleError(rc, "csr_transpose")
+    return ioff, iidx, iw
+
+
 def stable_marriage(men_pref, women_rank):
     """Man-proposing Gale-Shapley.  Returns (wife[m], husband[w], next[m], proposals)."""
     mp = _c(men_pref, np.int32); wr = _c(women_rank, np.int32)

@@ -129,6 +129,36 @@ int oracle_bfs(int32_t n, const int64_t *offsets, const int32_t *indices, int32_
     return OR_OK;
 }
 
+/* -------------------------------------------------------- Transpose
+ * In-arc CSR of a graph (input of the pull form of the BFS predicate,
+ * Sec. 4.2, which reads in-neighbours): in_offsets[v] = number of arcs whose
+ * target is below v; row v lists the sources of the arcs into v, in the order
+ * the arcs appear in the out-arc CSR (a stable counting sort by target).
+ * in_weights (may be NULL) carries each arc's weight along. */
+int oracle_csr_transpose(int32_t n, const int64_t *offsets, const int32_t *indices, const uint32_t *weights,
+                         int64_t *in_offsets, int32_t *in_indices, uint32_t *in_weights) {
+    if (n < 1) return OR_ERR_ARG;
+    int64_t m = offsets[n];
+    for (int32_t v = 0; v <= n; v++) in_offsets[v] = 0;
+    for (int64_t e = 0; e < m; e++) {
+        if (indices[e] < 0 || indices[e] >= n) return OR_ERR_ARG;
+        in_offsets[indices[e] + 1]++;
+    }
+    for (int32_t v = 0; v < n; v++) in_offsets[v + 1] += in_offsets[v];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    if (!fill) return OR_ERR_NOMEM;
+    for (int32_t v = 0; v < n; v++) fill[v] = in_offsets[v];
+    for (int32_t u = 0; u < n; u++) {
+        for (int64_t e = offsets[u]; e < offsets[u + 1]; e++) {
+            int64_t pos = fill[indices[e]]++;
+            in_indices[pos] = u;
+            if (in_weights) in_weights[pos] = weights[e];
+        }
+    }
+    free(fill);
+    return OR_OK;
+}
+
 /* ------------------------------------------------------- Gale-Shapley */
 
 /* men_pref[m*n+k] = k-th most preferred woman of man m;

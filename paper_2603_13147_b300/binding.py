@@ -43,7 +43,7 @@ class Sched(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("delta", ctypes.c_uint32), ("block_cfg", ctypes.c_int32),
                 ("dense_permille", ctypes.c_int32), ("use_mlp", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("deadline_ns", ctypes.c_int64), ("mlp_params", ctypes.c_void_p), ("local_chain", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("pull_permille", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -51,7 +51,7 @@ class Stats(ctypes.Structure):
                 ("edges", ctypes.c_int64), ("advances", ctypes.c_int64), ("aux", ctypes.c_int64),
                 ("elapsed_ns", ctypes.c_int64), ("mode_used", ctypes.c_int32), ("delta_used", ctypes.c_uint32),
                 ("block_cfg_used", ctypes.c_int32), ("dense_sweeps", ctypes.c_int32),
-                ("local_chain_used", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("local_chain_used", ctypes.c_int32), ("pull_sweeps", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,7 +71,8 @@ def lib() -> ctypes.CDLL:
         L.llp_status_string.restype = ctypes.c_char_p
         for name in ("llp_sssp_workspace_size", "llp_bfs_workspace_size", "llp_stable_marriage_workspace_size",
                      "llp_knapsack_workspace_size", "llp_transitive_closure_workspace_size",
-                     "llp_job_schedule_workspace_size", "llp_reduce_workspace_size"):
+                     "llp_job_schedule_workspace_size", "llp_reduce_workspace_size",
+                     "llp_csr_transpose_workspace_size"):
             if hasattr(L, name):
                 getattr(L, name).restype = ctypes.c_size_t
         _lib = L
@@ -87,9 +88,10 @@ def status_string(code: int) -> str:
 
 
 def make_sched(mode=0, delta=0, block_cfg=0, dense_permille=0, use_mlp=0, threads=0, deadline_ns=0,
-               mlp_params=None, local_chain=0) -> Sched:
+               mlp_params=None, local_chain=0, pull_permille=0) -> Sched:
     s = Sched()
     s.local_chain = local_chain
+    s.pull_permille = pull_permille
     s.mode, s.delta, s.block_cfg, s.dense_permille = mode, delta, block_cfg, dense_permille
     s.use_mlp, s.threads, s.deadline_ns = use_mlp, threads, deadline_ns
     s.mlp_params = None if mlp_params is None else mlp_params.data_ptr()
@@ -166,6 +168,28 @@ class DeviceGraph:
         c.weights = None if self.weights is None else self.weights.data_ptr()
         return c
 
+    def transpose(self, with_weights: bool = False, ws=None, stream=None) -> "DeviceGraph":
+        """The in-arc CSR (llp_csr_transpose): row v lists the sources of the arcs into v,
+        in an unspecified order; same offset type."""
+        dev = self.indices.device
+        off = torch.empty(self.n + 1, dtype=self.offsets.dtype, device=dev)
+        idx = torch.empty(self.m, dtype=torch.int32, device=dev)
+        w = None
+        if with_weights:
+            if self.weights is None:
+                raise ValueError("graph has no weights")
+            w = torch.empty(self.m, dtype=self.weights.dtype, device=dev)
+        if ws is None:
+            ws = workspace(lib().llp_csr_transpose_workspace_size(ctypes.c_int32(self.n), ctypes.c_int64(self.m)),
+                           dev)
+        c = self.csr()
+        rc = lib().llp_csr_transpose(ctypes.byref(c), _ptr(off), _ptr(idx), _ptr(w), _ptr(ws),
+                                     ctypes.c_size_t(ws.numel()), _stream(stream))
+        _check(rc, "llp_csr_transpose")
+        t = DeviceGraph(off, idx, w)
+        t.transpose_ws = ws
+        return t
+
 
 def sssp_workspace_size(n: int, m: int) -> int:
     return int(lib().llp_sssp_workspace_size(ctypes.c_int32(n), ctypes.c_int64(m)))
@@ -199,6 +223,22 @@ def sssp(g: DeviceGraph, source: int, out=None, sched: Sched | None = None, ws=N
 def bfs(g: DeviceGraph, source: int, out=None, sched: Sched | None = None, ws=None, stream=None):
     """BFS levels (uint32 bit patterns in int32; 0xFFFFFFFF = unreachable).  Returns (level, workspace)."""
     return _graph_call(lib().llp_bfs, bfs_workspace_size, g, source, out, sched, ws, stream, "llp_bfs")
+
+
+def bfs_pull(g: DeviceGraph, g_in: DeviceGraph, source: int, out=None, sched: Sched | None = None, ws=None,
+             stream=None):
+    """BFS with direction switching (llp_bfs_pull); g_in = g.transpose().  Returns (level, workspace)."""
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.int32, device=g.indices.device)
+    _dev(out, torch.int32, "out")
+    if ws is None:
+        ws = workspace(bfs_workspace_size(g.n, g.m), g.indices.device)
+    c, ci = g.csr(), g_in.csr()
+    rc = lib().llp_bfs_pull(ctypes.byref(c), ctypes.byref(ci), ctypes.c_int32(source), _ptr(out),
+                            None if sched is None else ctypes.byref(sched), _ptr(ws), ctypes.c_size_t(ws.numel()),
+                            _stream(stream))
+    _check(rc, "llp_bfs_pull")
+    return out, ws
 
 
 def as_u32(t: torch.Tensor):

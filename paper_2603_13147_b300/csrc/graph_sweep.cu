@@ -34,6 +34,13 @@
 //     worklist; the others wait in a far list filtered when the near worklist
 //     empties.
 // The run stops when no index is forbidden: every worklist is empty.
+//
+// BFS with the transpose (llp_bfs_pull) may evaluate a wide sweep pull-style:
+// every vertex not reached yet scans its in-arcs and stops at the first source
+// in the frontier bitmap.  Such a sweep reads the frontier at random, so it
+// cannot clear it as it goes; three bitmaps rotate by sweep (k mod 3) and the
+// one a pull sweep left behind is cleared during the following sweep, which
+// neither reads nor writes it.
 #include <algorithm>
 #include <mutex>
 
@@ -74,7 +81,12 @@ struct GraphArgs {
     uint32_t *dist;                 // output
     unsigned long long *key;        // d << 32 | class during the run
     uint2 *cls;      // per 32 vertices: x = has out-arcs, y = large
-    uint32_t *bm[2]; // frontier bitmaps by sweep parity
+    uint32_t *bm[3]; // frontier bitmaps, B_k = bm[k % 3]
+    // pull sweeps (BFS only): in-arcs, visited bitmap, frontier size that selects them
+    const OffT *in_off;              // NULL: push only
+    const int32_t *in_idx;
+    uint32_t *vis;                   // valid after a pull sweep: bit set = level known
+    unsigned long long pull_arcs;
     int32_t *small[2];
     int2 *chunk[2];
     int2 *far[2];
@@ -99,6 +111,8 @@ struct SweepCtx {
     unsigned long long bucket_hi;  // exclusive bound of the current bucket
     uint32_t fa;                   // far-list generation
     bool dense_next;               // small advances only set their bitmap bit
+    bool pull = false;             // this sweep runs over the in-arcs
+    bool vis_valid = false;        // a.vis holds every vertex reached so far
     // local chaining (recency-biased per-warp bag): advanced small vertices are
     // expanded by the same warp within the sweep, LIFO, from a shared-memory stack
     int32_t *lq;
@@ -145,53 +159,13 @@ __device__ __forceinline__ void red_min64(unsigned long long *p, unsigned long l
 
 __device__ __forceinline__ uint32_t key_dist(unsigned long long kv) { return (uint32_t)(kv >> 32); }
 
-// Put the advanced vertices v[j] (want[j], class cls[j]) into the worklist of
-// sweep k+1, all kUnroll of them at once.  Warp-collective.
+// Append the vertices v[j] that entered the frontier bitmap of sweep k+1 for
+// the first time (newly[j]) to the small-vertex list or, as chunks, to the
+// chunk list of sweep k+1, through the warp's staging buffers.  Warp-collective.
 template <typename OffT, int U>
-__device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, const bool (&want_in)[U], const int32_t (&v)[U],
-                                          const uint32_t (&cls)[U], SweepCtx &c) {
-    bool want[U];
-#pragma unroll
-    for (int j = 0; j < U; j++) want[j] = want_in[j];
-    if (c.chain_on) {
-        // small advances stay with this warp when its stack has room for all of them
-        uint32_t nl = 0;
-#pragma unroll
-        for (int j = 0; j < U; j++) nl += (want[j] && cls[j] == 1);
-        uint32_t incl = nl;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane_id() >= o) incl += t;
-        }
-        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-        if (tot > 0 && c.lq_n + tot <= kLocalQ) {
-            uint32_t slot = c.lq_n + incl - nl;
-#pragma unroll
-            for (int j = 0; j < U; j++)
-                if (want[j] && cls[j] == 1) {
-                    c.lq[slot++] = v[j];
-                    want[j] = false;
-                }
-            c.lq_n += tot;
-        }
-    }
-    bool newly[U];
+__device__ __forceinline__ void append_new(const GraphArgs<OffT> &a, const bool (&newly)[U], const int32_t (&v)[U],
+                                           const uint32_t (&cls)[U], SweepCtx &c) {
     uint32_t n_small = 0, n_large = 0;
-#pragma unroll
-    for (int j = 0; j < U; j++) {
-        newly[j] = false;
-        if (want[j] && cls[j] != 0) {
-            const uint32_t bit = 1u << (v[j] & 31);
-            uint32_t *word = c.bm_next + (v[j] >> 5);
-            if (c.dense_next && cls[j] == 1) {
-                red_or(word, bit);
-                c.marked++;
-            } else {
-                newly[j] = (atomicOr(word, bit) & bit) == 0;
-            }
-        }
-    }
     uint32_t nch[U];
 #pragma unroll
     for (int j = 0; j < U; j++) {
@@ -251,6 +225,55 @@ __device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, const bool (
             c.st_nc += tot;
         }
     }
+}
+
+// Put the advanced vertices v[j] (want[j], class cls[j]) into the worklist of
+// sweep k+1, all kUnroll of them at once.  Warp-collective.
+template <typename OffT, int U>
+__device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, const bool (&want_in)[U], const int32_t (&v)[U],
+                                          const uint32_t (&cls)[U], SweepCtx &c) {
+    bool want[U];
+#pragma unroll
+    for (int j = 0; j < U; j++) want[j] = want_in[j];
+    if (c.chain_on) {
+        // small advances stay with this warp when its stack has room for all of them
+        uint32_t nl = 0;
+#pragma unroll
+        for (int j = 0; j < U; j++) nl += (want[j] && cls[j] == 1);
+        uint32_t incl = nl;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane_id() >= o) incl += t;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (tot > 0 && c.lq_n + tot <= kLocalQ) {
+            uint32_t slot = c.lq_n + incl - nl;
+#pragma unroll
+            for (int j = 0; j < U; j++)
+                if (want[j] && cls[j] == 1) {
+                    c.lq[slot++] = v[j];
+                    want[j] = false;
+                }
+            c.lq_n += tot;
+        }
+    }
+    bool newly[U];
+#pragma unroll
+    for (int j = 0; j < U; j++) {
+        newly[j] = false;
+        if (want[j] && cls[j] != 0) {
+            const uint32_t bit = 1u << (v[j] & 31);
+            uint32_t *word = c.bm_next + (v[j] >> 5);
+            if (c.dense_next && cls[j] == 1) {
+                red_or(word, bit);
+                c.marked++;
+            } else {
+                newly[j] = (atomicOr(word, bit) & bit) == 0;
+            }
+        }
+    }
+    append_new(a, newly, v, cls, c);
 }
 
 // Evaluate forbidden(v) against candidate distances and advance, for up to
@@ -475,6 +498,174 @@ __device__ __forceinline__ void scan_words(const GraphArgs<OffT> &a, int64_t g, 
     }
 }
 
+// ---- pull sweeps (BFS over in-arcs; levels are exact per sweep, so the first
+// in-neighbour found in the frontier B_k gives the least level k)
+constexpr int kPullLaneRounds = 2;  // per-lane rounds of kUnroll in-arcs before the warp helps
+
+// Up to 32 unreached vertices, one per lane (ok), v in bitmap word slot `owner`
+// of the item.  Each lane scans its in-arcs kUnroll at a time and stops at
+// the first source u with u in B_k; a vertex still open after
+// kPullLaneRounds rounds is finished by the whole warp, 32 * kUnroll in-arcs
+// per step.  A vertex found gets level d(u) + 1 and enters B_{k+1} (if it has
+// out-arcs) and the worklists of sweep k+1.  Warp-collective.
+template <typename OffT>
+__device__ __forceinline__ void pull_batch(const GraphArgs<OffT> &a, bool ok, int32_t v, int owner, SweepCtx &c,
+                                           uint32_t *s_found) {
+    OffT b = 0, e = 0;
+    if (ok) {
+        b = __ldg(a.in_off + v);
+        e = __ldg(a.in_off + v + 1);
+    }
+    c.items += ok;
+    bool found = false;
+    int32_t par = 0;
+    uint32_t exam = 0;
+#pragma unroll
+    for (int r = 0; r < kPullLaneRounds; r++) {
+        const bool act = ok && !found && b < e;
+        if (!__any_sync(0xffffffffu, act)) break;
+        int32_t u[kUnroll];
+        bool in[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) {
+            in[j] = act && b + (OffT)j < e;
+            u[j] = in[j] ? __ldg(a.in_idx + b + j) : 0;
+        }
+        uint32_t fw[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) fw[j] = in[j] ? __ldcg(c.bm_cur + (u[j] >> 5)) : 0u;
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) {
+            if (in[j] && !found) {
+                exam++;
+                if ((fw[j] >> (u[j] & 31)) & 1u) {
+                    found = true;
+                    par = u[j];
+                }
+            }
+        }
+        if (act) b = (e - b > (OffT)kUnroll) ? b + (OffT)kUnroll : e;
+    }
+    uint32_t rest = __ballot_sync(0xffffffffu, ok && !found && b < e);
+    while (rest) {
+        const int l = __ffs(rest) - 1;
+        rest &= rest - 1u;
+        const OffT bl = __shfl_sync(0xffffffffu, b, l);
+        const OffT el = __shfl_sync(0xffffffffu, e, l);
+        int32_t hit = -1;
+        uint32_t seen = 0;
+        for (OffT base = bl; base < el && hit < 0; base += 32 * kUnroll) {
+            int32_t u[kUnroll];
+            bool in[kUnroll];
+#pragma unroll
+            for (int j = 0; j < kUnroll; j++) {
+                const OffT x = base + (OffT)(32 * j + lane_id());
+                in[j] = x < el;
+                u[j] = in[j] ? __ldg(a.in_idx + x) : 0;
+            }
+            uint32_t fw[kUnroll];
+#pragma unroll
+            for (int j = 0; j < kUnroll; j++) fw[j] = in[j] ? __ldcg(c.bm_cur + (u[j] >> 5)) : 0u;
+#pragma unroll
+            for (int j = 0; j < kUnroll; j++) {
+                const uint32_t bal = __ballot_sync(0xffffffffu, in[j] && ((fw[j] >> (u[j] & 31)) & 1u));
+                if (bal && hit < 0) hit = __shfl_sync(0xffffffffu, u[j], __ffs(bal) - 1);
+            }
+            seen += (uint32_t)min((OffT)(32 * kUnroll), el - base);
+        }
+        if (lane_id() == l) {
+            exam += seen;
+            if (hit >= 0) {
+                found = true;
+                par = hit;
+            }
+        }
+    }
+    c.edges += exam;
+    uint32_t cls = 0;
+    if (found) {
+        const uint32_t dp = key_dist(__ldcg(a.key + par));
+        const uint2 cw = __ldg(&a.cls[(uint32_t)v >> 5]);
+        const uint32_t bit = 1u << (v & 31);
+        cls = (cw.x & bit) ? ((cw.y & bit) ? 2u : 1u) : 0u;
+        a.key[v] = ((unsigned long long)(dp + 1u) << 32) | cls;
+        atomicOr(&s_found[owner], bit);
+        c.adv++;
+    }
+    const bool nw[1] = {found && cls != 0};
+    const int32_t vv[1] = {v};
+    const uint32_t cc[1] = {cls};
+    append_new(a, nw, vv, cc, c);
+}
+
+// Pull sweep item: kGroupWords bitmap words.  The vertices not reached yet
+// (from the visited bitmap, or from their distances on the first pull sweep
+// after push sweeps) are compacted 32 per batch; afterwards the item's words
+// of the visited bitmap and of B_{k+1} are written whole (no other warp owns
+// them in this sweep).
+template <typename OffT>
+__device__ __forceinline__ void pull_words(const GraphArgs<OffT> &a, int64_t g, SweepCtx &c, uint32_t *s_found) {
+    const int64_t w0 = g * kGroupWords;
+    const int q = lane_id();
+    uint32_t unv = 0;  // lane q < kGroupWords: vertices of word w0 + q not reached yet
+    if (c.vis_valid) {
+        if (q < kGroupWords && w0 + q < a.nwords) {
+            unv = ~__ldcg(a.vis + w0 + q);
+            const int64_t left = (int64_t)a.n - (w0 + q) * 32;
+            if (left < 32) unv &= (1u << left) - 1u;
+        }
+    } else {
+        unsigned long long kv[kGroupWords];
+#pragma unroll
+        for (int j = 0; j < kGroupWords; j++) {
+            const int64_t v = (w0 + j) * 32 + q;
+            kv[j] = v < a.n ? __ldcg(a.key + v) : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < kGroupWords; j++) {
+            const int64_t v = (w0 + j) * 32 + q;
+            const uint32_t b = __ballot_sync(0xffffffffu, v < a.n && key_dist(kv[j]) == kInf);
+            if (q == j) unv = b;
+        }
+    }
+    if (q < kGroupWords) s_found[q] = 0u;
+    __syncwarp();
+    const uint32_t cnt = __popc(unv);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < kGroupWords; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (q >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, kGroupWords - 1);
+    const uint32_t excl = incl - cnt;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t t = base + q;
+        int pos = 0;
+#pragma unroll
+        for (int sh = kGroupWords / 2; sh > 0; sh >>= 1) {
+            const uint32_t probe = __shfl_sync(0xffffffffu, incl, pos + sh - 1);
+            if (probe <= t) pos += sh;
+        }
+        const bool ok = t < total;
+        const int owner = ok ? pos : 0;
+        const uint32_t ex = __shfl_sync(0xffffffffu, excl, owner);
+        const uint32_t word = __shfl_sync(0xffffffffu, unv, owner);
+        int32_t v = 0;
+        if (ok) v = (int32_t)((w0 + owner) * 32 + __fns(word, 0, (int)(t - ex) + 1));
+        pull_batch(a, ok, v, owner, c, s_found);
+    }
+    __syncwarp();
+    if (q < kGroupWords && w0 + q < a.nwords) {
+        const int64_t wi = w0 + q;
+        const uint32_t f = s_found[q];
+        if (!c.vis_valid || f) a.vis[wi] = ~unv | f;
+        const uint32_t nb = f & __ldg(&a.cls[wi].x);
+        if (nb) c.bm_next[wi] = nb;
+    }
+    __syncwarp();
+}
+
 // End of a sweep: the CTA publishes every warp's staged list entries with one
 // reservation per list, and adds its dense_next mark count.
 struct BlockFlush {
@@ -524,7 +715,9 @@ __device__ __forceinline__ void flush_sweep(const GraphArgs<OffT> &a, SweepCtx &
     c.st_nc = 0;
 }
 
-template <typename OffT, bool UNIT>
+// PULL: BFS with in-arcs (llp_bfs_pull); a separate instantiation keeps the
+// pull code out of the register allocation of the push-only kernels.
+template <typename OffT, bool UNIT, bool PULL>
 __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) {
     __shared__ BlockFlush s_flush;
     __shared__ uint32_t s_work[2];
@@ -588,6 +781,7 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
                 a.cls[wi] = make_uint2(has, large);
                 a.bm[0][wi] = 0u;
                 a.bm[1][wi] = 0u;
+                a.bm[2][wi] = 0u;
             }
         }
     }
@@ -625,11 +819,17 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
     c.k = 1;
     c.fa = 0;
     c.bucket_hi = (c.delta == kInf) ? (1ull << 40) : (unsigned long long)c.delta;
-    uint32_t dense_sweeps = 0;
+    uint32_t dense_sweeps = 0, pull_sweeps = 0;
+    bool prev_pull = false;
     while (alive) {
         const uint32_t k = c.k;
-        c.bm_cur = a.bm[k & 1];
-        c.bm_next = a.bm[(k + 1) & 1];
+        c.bm_cur = a.bm[k % 3];
+        c.bm_next = a.bm[(k + 1) % 3];
+        if (prev_pull) {
+            // B_{k-1} was read, not consumed, by the pull sweep k-1; it becomes B_{k+2}
+            uint32_t *spare = a.bm[(k + 2) % 3];
+            for (int64_t wi = gtid; wi < a.nwords; wi += gthreads) spare[wi] = 0u;
+        }
         const uint32_t ns = *(volatile uint32_t *)&h->n_small[k % 3];
         const uint32_t nc = *(volatile uint32_t *)&h->n_chunk[k % 3];
         const bool dense = *(volatile uint32_t *)&h->list_ok[k % 3] == 0;
@@ -637,6 +837,8 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
                                         (unsigned long long)nc * (unsigned long long)c.chunk_edges;
         c.dense_next = c.mode == LLP_MODE_DENSE || (c.mode == LLP_MODE_AUTO && arcs > a.dense_arcs);
         if (ns + nc == 0) c.dense_next = false;
+        c.pull = PULL && UNIT && c.chain == 0 && ns + nc > 0 && arcs > a.pull_arcs;
+        if (c.pull) c.dense_next = false;  // a pull sweep appends every vertex it reaches
         if (threadIdx.x == 0) s_work[(k + 1) & 1] = 0;  // used after the next grid barrier
         if (gtid == 0) {
             const uint32_t r = (k + 2) % 3;
@@ -697,6 +899,18 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
             }
             c.bucket_hi = nh;
             c.fa += 1;
+        } else if (PULL && c.pull) {
+            pull_sweeps++;
+            const uint32_t ngroups = (uint32_t)(((int64_t)a.nwords + kGroupWords - 1) / kGroupWords);
+            uint32_t *s_found = reinterpret_cast<uint32_t *>(s_lq[threadIdx.x >> 5]);  // no local chain in pull runs
+            for (;;) {
+                uint32_t j = 0;
+                if (lane_id() == 0) j = atomicAdd(&s_work[k & 1], 1u);
+                j = __shfl_sync(0xffffffffu, j, 0);
+                const uint64_t g64 = (uint64_t)blockIdx.x + (uint64_t)j * gridDim.x;
+                if (g64 >= ngroups) break;
+                pull_words(a, (int64_t)g64, c, s_found);
+            }
         } else {
             dense_sweeps += dense;
             // chunks: static round robin (uniform cost, <= chunk_edges arcs)
@@ -737,6 +951,9 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
             c.chain_on = false;
         }
         flush_sweep(a, c, &s_flush);
+        prev_pull = c.pull;
+        c.vis_valid = c.pull;  // push sweeps reach vertices without recording them in vis
+        c.pull = false;
         alive = grid_barrier(h, phase, deadline);
         c.k += 1;
     }
@@ -754,6 +971,7 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
     if (gtid == 0) {
         h->sweeps = (int32_t)c.k;
         h->dense_sweeps = (int32_t)dense_sweeps;
+        h->scratch[9] = pull_sweeps;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -766,7 +984,8 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
 struct Layout {
     unsigned long long *key;
     uint2 *cls;
-    uint32_t *bm[2];
+    uint32_t *bm[3];
+    uint32_t *vis;
     int32_t *small[2];
     int2 *chunk[2];
     int2 *far[2];
@@ -785,6 +1004,8 @@ Layout carve_graph(void *ws, int32_t n, int64_t m) {
     L.cls = c.take<uint2>(nwords);
     L.bm[0] = c.take<uint32_t>(nwords);
     L.bm[1] = c.take<uint32_t>(nwords);
+    L.bm[2] = c.take<uint32_t>(nwords);
+    L.vis = c.take<uint32_t>(nwords);
     L.small[0] = c.take<int32_t>(n);
     L.small[1] = c.take<int32_t>(n);
     L.chunk[0] = c.take<int2>(chunk_cap);
@@ -814,8 +1035,11 @@ void resolve_schedule(const llp_sched_t *s, bool unit, int32_t n, int64_t m, int
 
 template <bool UNIT>
 llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, const llp_sched_t *s, void *ws,
-                         size_t ws_bytes, cudaStream_t stream) {
+                         size_t ws_bytes, cudaStream_t stream, const llp_csr_t *gin = nullptr) {
     if (!g || !out || !ws) return LLP_ERR_INVALID_ARG;
+    if (gin && (gin->n != g->n || gin->m != g->m || gin->offsets_64 != g->offsets_64 || !gin->offsets ||
+                (gin->m > 0 && !gin->indices)))
+        return LLP_ERR_INVALID_ARG;
     if (g->n < 1 || g->n > (1 << 29) || g->m < 0 || !g->offsets) return LLP_ERR_INVALID_ARG;
     if (g->m > 0 && (!g->indices || (!UNIT && !g->weights))) return LLP_ERR_INVALID_ARG;
     if (!g->offsets_64 && g->m > 0x7FFFFFFFll) return LLP_ERR_INVALID_ARG;
@@ -833,6 +1057,10 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
     llp_status_t rc = reset_header(ws, stream);
     if (rc != LLP_OK) return rc;
     const bool learned = s && s->use_mlp && s->mlp_params;
+    // pull sweeps: frontiers above m * permille / 1000 out-arcs (estimated as in AUTO mode)
+    const int ppm = s ? s->pull_permille : 0;
+    const bool pull_on = UNIT && gin && ppm >= 0;
+    const unsigned long long pull_arcs = (unsigned long long)g->m * (unsigned long long)(ppm > 0 ? ppm : 200) / 1000ull;
     if (learned) {
         rc = enqueue_learned_schedule(g, source, UNIT, s->mlp_params, (WsHeader *)ws, stream);
         if (rc != LLP_OK) return rc;
@@ -849,6 +1077,10 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         args.cls = L.cls;
         args.bm[0] = L.bm[0];
         args.bm[1] = L.bm[1];
+        args.bm[2] = L.bm[2];
+        args.vis = L.vis;
+        args.in_idx = pull_on ? gin->indices : nullptr;
+        args.pull_arcs = pull_arcs;
         args.small[0] = L.small[0];
         args.small[1] = L.small[1];
         args.chunk[0] = L.chunk[0];
@@ -871,14 +1103,24 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         GraphArgs<int64_t> args;
         fill(args);
         args.off = (const int64_t *)g->offsets;
+        args.in_off = pull_on ? (const int64_t *)gin->offsets : nullptr;
         void *kargs[] = {&args};
-        return launch_cooperative((const void *)graph_sweep_kernel<int64_t, UNIT>, threads, 0, 0, kargs, stream);
+        const void *fn = (const void *)graph_sweep_kernel<int64_t, UNIT, false>;
+        if constexpr (UNIT) {
+            if (pull_on) fn = (const void *)graph_sweep_kernel<int64_t, true, true>;
+        }
+        return launch_cooperative(fn, threads, 0, 0, kargs, stream);
     } else {
         GraphArgs<int32_t> args;
         fill(args);
         args.off = (const int32_t *)g->offsets;
+        args.in_off = pull_on ? (const int32_t *)gin->offsets : nullptr;
         void *kargs[] = {&args};
-        return launch_cooperative((const void *)graph_sweep_kernel<int32_t, UNIT>, threads, 0, 0, kargs, stream);
+        const void *fn = (const void *)graph_sweep_kernel<int32_t, UNIT, false>;
+        if constexpr (UNIT) {
+            if (pull_on) fn = (const void *)graph_sweep_kernel<int32_t, true, true>;
+        }
+        return launch_cooperative(fn, threads, 0, 0, kargs, stream);
     }
 }
 
@@ -953,6 +1195,12 @@ llp_status_t llp_sssp(const llp_csr_t *g, int32_t source, uint32_t *dist, const 
 llp_status_t llp_bfs(const llp_csr_t *g, int32_t source, uint32_t *level, const llp_sched_t *sched, void *ws,
                      size_t ws_bytes, void *stream) {
     return llp::graph_solve<true>(g, source, level, sched, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+llp_status_t llp_bfs_pull(const llp_csr_t *g, const llp_csr_t *g_in, int32_t source, uint32_t *level,
+                          const llp_sched_t *sched, void *ws, size_t ws_bytes, void *stream) {
+    if (!g_in) return LLP_ERR_INVALID_ARG;
+    return llp::graph_solve<true>(g, source, level, sched, ws, ws_bytes, (cudaStream_t)stream, g_in);
 }
 
 }  // extern "C"

@@ -68,3 +68,36 @@ def test_invalid_arguments_rejected_on_host(L):
     # m > 0 without indices
     c.m = 5
     assert L.llp_bfs(ctypes.byref(c), 0, out, None, ws, ctypes.c_size_t(1 << 30), None) == llp.LLP_ERR_INVALID_ARG
+
+
+def test_pull_and_transpose_arguments_rejected_on_host(L):
+    import paper_2603_13147_b300 as llp
+    c = llp.Csr()
+    c.n, c.m = 10, 0
+    c.offsets = 0x1000
+    t = llp.Csr()
+    t.n, t.m = 10, 0
+    t.offsets = 0x3000
+    ws = ctypes.c_void_p(0x100000)
+    out = ctypes.c_void_p(0x200000)
+    big = ctypes.c_size_t(1 << 30)
+    # missing transpose, or one that does not match the graph
+    assert L.llp_bfs_pull(ctypes.byref(c), None, 0, out, None, ws, big, None) == llp.LLP_ERR_INVALID_ARG
+    for field, val in (("n", 11), ("m", 3), ("offsets_64", 1), ("offsets", None)):
+        bad = llp.Csr()
+        ctypes.pointer(bad)[0] = t
+        setattr(bad, field, val)
+        assert L.llp_bfs_pull(ctypes.byref(c), ctypes.byref(bad), 0, out, None, ws, big, None) == \
+            llp.LLP_ERR_INVALID_ARG, field
+    assert L.llp_bfs_pull(ctypes.byref(c), ctypes.byref(t), 10, out, None, ws, big, None) == llp.LLP_ERR_INVALID_ARG
+    # transpose: NULL outputs, misaligned or small workspace
+    L.llp_csr_transpose_workspace_size.restype = ctypes.c_size_t
+    assert L.llp_csr_transpose_workspace_size(ctypes.c_int32(10), ctypes.c_int64(0)) > 4096
+    assert L.llp_csr_transpose(ctypes.byref(c), None, None, None, ws, big, None) == llp.LLP_ERR_INVALID_ARG
+    assert L.llp_csr_transpose(ctypes.byref(c), out, None, None, ctypes.c_void_p(0x100004), big,
+                               None) == llp.LLP_ERR_INVALID_ARG
+    assert L.llp_csr_transpose(ctypes.byref(c), out, None, None, ws, ctypes.c_size_t(64),
+                               None) == llp.LLP_ERR_WORKSPACE_TOO_SMALL
+    c.m = 5  # arcs but no indices
+    assert L.llp_csr_transpose(ctypes.byref(c), out, ctypes.c_void_p(0x300000), None, ws, big,
+                               None) == llp.LLP_ERR_INVALID_ARG

@@ -202,3 +202,150 @@ def test_rmat22_bfs_full(llp, rmat22):
     assert (d == ref).all()
     d64, _ = run_bfs(llp, g, s, offsets_64=True)
     assert (d64 == ref).all()
+
+
+# ----------------------------------------------- BFS with pull sweeps (in-arcs)
+
+def run_bfs_pull(llp, g, s, **kw):
+    dg = dev_graph(llp, g, kw.pop("offsets_64", False))
+    gt = dg.transpose()
+    sched = llp.make_sched(**kw) if kw else None
+    d, ws = llp.bfs_pull(dg, gt, s, sched=sched)
+    st = llp.get_status(ws)
+    assert st["status"] == 0, st
+    return llp.as_u32(d), st
+
+
+def check_transpose(llp, g, offsets_64):
+    dg = dev_graph(llp, g, offsets_64)
+    gt = dg.transpose(with_weights=g.get("weights") is not None)
+    ws = gt.transpose_ws
+    assert llp.get_status(ws)["status"] == 0
+    ioff, iidx, iw = oracle.csr_transpose(g["offsets"], g["indices"], g.get("weights"))
+    off = gt.offsets.cpu().numpy()
+    assert off.dtype == (np.int64 if offsets_64 else np.int32)
+    assert (off.astype(np.int64) == ioff).all()
+    idx = gt.indices.cpu().numpy()
+    w = gt.weights.cpu().numpy().view(np.uint32) if gt.weights is not None else np.zeros_like(idx)
+    rw = iw if iw is not None else np.zeros_like(iidx)
+    # rows as multisets of (source, weight): the order within a row is unspecified
+    row = np.repeat(np.arange(g["n"]), np.diff(ioff))
+    a = np.lexsort((w.astype(np.int64), idx, row))
+    b = np.lexsort((rw.astype(np.int64), iidx, row))
+    assert (idx[a] == iidx[b]).all() and (w[a] == rw[b]).all()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_transpose_matches_oracle(llp, seed):
+    rng = np.random.default_rng(400 + seed)
+    n = int(rng.integers(1, 5000))
+    arcs = [(int(rng.integers(n)), int(rng.integers(n)), int(rng.integers(1, 1000)))
+            for _ in range(int(rng.integers(0, 8 * n)))]
+    arcs += [(int(rng.integers(n)), 0, 7) for _ in range(int(rng.integers(0, 3000)))]  # a high in-degree target
+    check_transpose(llp, csr_from_arcs(n, arcs), bool(seed % 2))
+
+
+def test_transpose_rmat16(llp):
+    check_transpose(llp, synth.rmat(16, seed=21), False)
+
+
+PULL_SCHEDS = [dict(), dict(pull_permille=1), dict(pull_permille=-1), dict(pull_permille=1, mode=2),
+               dict(pull_permille=1, block_cfg=1), dict(pull_permille=5, block_cfg=3, threads=256),
+               dict(pull_permille=1, mode=1, block_cfg=3), dict(pull_permille=1, local_chain=4)]
+
+
+@pytest.mark.parametrize("kw", PULL_SCHEDS)
+def test_bfs_pull_er16k(llp, kw):
+    g = synth.er16k()
+    d, st = run_bfs_pull(llp, g, 0, **kw)
+    assert (d == oracle.bfs(g["offsets"], g["indices"], 0)).all()
+    if kw.get("pull_permille") == 1 and not kw.get("local_chain"):
+        # every sweep pulls except the first (the source alone is below m / 1000 arcs) and the
+        # last (empty frontier)
+        assert st["pull_sweeps"] == st["sweeps"] - 2 > 0
+    if kw.get("pull_permille") == -1 or kw.get("local_chain"):
+        assert st["pull_sweeps"] == 0
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_bfs_pull_random_ragged(llp, seed):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(1, 4000))
+    arcs = [(int(rng.integers(n)), int(rng.integers(n)), 1) for _ in range(int(rng.integers(0, 6 * n)))]
+    for h in range(min(3, n)):  # hubs: large out-degree and large in-degree
+        arcs += [(h, int(rng.integers(n)), 1) for _ in range(int(rng.integers(0, 1500)))]
+        arcs += [(int(rng.integers(n)), n - 1 - h, 1) for _ in range(int(rng.integers(0, 1500)))]
+    g = csr_from_arcs(n, arcs)
+    s = int(rng.integers(n))
+    ref = oracle.bfs(g["offsets"], g["indices"], s)
+    for kw in (dict(), dict(pull_permille=1), dict(pull_permille=20, block_cfg=1)):
+        d, _ = run_bfs_pull(llp, g, s, offsets_64=bool(seed % 2), **kw)
+        assert (d == ref).all(), kw
+
+
+def test_bfs_pull_push_pull_alternation(llp):
+    """Wide, narrow, wide frontiers: pull, push, pull.  The push sweep between them reaches
+    vertices (a ring) that the second pull sweep must see as reached."""
+    L = 1000
+    X = L + 1
+    arcs = [(0, 1 + i, 1) for i in range(L)] + [(1 + i, X, 1) for i in range(L)]
+    arcs += [(X, X + 1 + i, 1) for i in range(L)]
+    arcs += [(X + 1 + i, X + 1 + (i + 1) % L, 1) for i in range(L)]
+    arcs += [(X + 1 + i, X + 1 + L + i, 1) for i in range(L)]
+    n = X + 1 + 2 * L
+    g = csr_from_arcs(n, arcs)
+    d, st = run_bfs_pull(llp, g, 0, pull_permille=300)
+    assert (d == oracle.bfs(g["offsets"], g["indices"], 0)).all()
+    assert st["pull_sweeps"] == 2
+    assert d[X] == 2 and d[X + 1] == 3 and d[n - 1] == 4
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(pull_permille=1)])
+def test_bfs_pull_grid(llp, kw):
+    g = synth.grid_graph(96, 77, 1, 1000, seed=5)
+    d, _ = run_bfs_pull(llp, g, 5, **kw)
+    assert (d == oracle.bfs(g["offsets"], g["indices"], 5)).all()
+
+
+@pytest.mark.parametrize("n", [31, 33, 1023, 1025])
+def test_bfs_pull_ragged_vertex_counts(llp, n):
+    rng = np.random.default_rng(n + 1)
+    arcs = [(int(rng.integers(n)), int(rng.integers(n)), 1) for _ in range(4 * n)]
+    arcs += [(n - 1, int(rng.integers(n)), 1) for _ in range(70)]
+    g = csr_from_arcs(n, arcs)
+    for kw in (dict(pull_permille=1), dict()):
+        d, _ = run_bfs_pull(llp, g, n - 1, **kw)
+        assert (d == oracle.bfs(g["offsets"], g["indices"], n - 1)).all()
+
+
+def test_bfs_pull_edge_cases(llp):
+    g = dict(n=1, m=0, offsets=np.zeros(2, np.int64), indices=np.zeros(0, np.int32), weights=None)
+    d, _ = run_bfs_pull(llp, g, 0, pull_permille=1)
+    assert d.tolist() == [0]
+    g = csr_from_arcs(5, [(1, 2, 1), (2, 3, 1)])  # source without out-arcs
+    d, _ = run_bfs_pull(llp, g, 0, pull_permille=1)
+    assert d.tolist() == [0] + [oracle.INF] * 4
+    g = csr_from_arcs(3, [(0, 0, 1), (0, 1, 1), (0, 1, 1), (1, 1, 1), (1, 2, 1), (1, 2, 1)])
+    d, _ = run_bfs_pull(llp, g, 0, pull_permille=1)
+    assert d.tolist() == [0, 1, 2]
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(pull_permille=10), dict(pull_permille=200, block_cfg=3)])
+def test_bfs_pull_rmat16(llp, kw):
+    g = synth.rmat(16, seed=21)
+    s = synth.max_out_degree_vertex(g)
+    d, st = run_bfs_pull(llp, g, s, **kw)
+    assert (d == oracle.bfs(g["offsets"], g["indices"], s)).all()
+    assert st["pull_sweeps"] >= 1
+
+
+def test_rmat22_bfs_pull_full(llp, rmat22):
+    """Full-size R-MAT scale 22 with its device transpose, default schedule as benchmarked."""
+    g = rmat22
+    s = synth.max_out_degree_vertex(g)
+    ref = oracle.bfs(g["offsets"], g["indices"], s)
+    d, st = run_bfs_pull(llp, g, s)
+    assert (d == ref).all()
+    assert st["pull_sweeps"] >= 1
+    d64, _ = run_bfs_pull(llp, g, s, offsets_64=True)
+    assert (d64 == ref).all()

@@ -211,3 +211,51 @@ def test_closure_chain_closed_form():
     off, idx, _ = csr_from_arcs(n, [(i, i + 1, 1) for i in range(n - 1)])
     R = unpack(oracle.transitive_closure(off, idx), n)
     assert (R == np.triu(np.ones((n, n), bool), 1)).all()
+
+
+# -------------------------------------------------------------- transpose
+
+@pytest.mark.parametrize("seed", range(10))
+def test_transpose_brute_force_tiny(seed):
+    """Row v of the in-arc CSR = the (source, weight) of every arc into v, in arc order."""
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(1, 9))
+    arcs = random_arcs(rng, n, int(rng.integers(0, 25)), 9)
+    off, idx, w = csr_from_arcs(n, arcs)
+    ioff, iidx, iw = oracle.csr_transpose(off, idx, w)
+    src = np.repeat(np.arange(n), np.diff(off))
+    for v in range(n):
+        want = [(int(src[e]), int(w[e])) for e in range(len(idx)) if idx[e] == v]
+        got = list(zip(iidx[ioff[v]:ioff[v + 1]].tolist(), iw[ioff[v]:ioff[v + 1]].tolist()))
+        assert got == want
+    assert ioff[0] == 0 and ioff[-1] == len(idx)
+
+
+def test_transpose_twice_sorts_rows():
+    """T(T(g)) is g with each row stably sorted by target."""
+    g = synth.rmat_graph(10, 8, seed=5)
+    ioff, iidx, iw = oracle.csr_transpose(g["offsets"], g["indices"], g["weights"])
+    off2, idx2, w2 = oracle.csr_transpose(ioff, iidx, iw)
+    assert (off2 == g["offsets"]).all()
+    for u in range(g["n"]):
+        a, b = g["offsets"][u], g["offsets"][u + 1]
+        order = np.argsort(g["indices"][a:b], kind="stable")
+        assert (idx2[a:b] == g["indices"][a:b][order]).all()
+        assert (w2[a:b] == g["weights"][a:b][order]).all()
+
+
+def test_transpose_reverses_reachability():
+    """v is reachable from s in g iff s is reachable from v in the transpose."""
+    rng = np.random.default_rng(9)
+    n = 60
+    off, idx, _ = csr_from_arcs(n, random_arcs(rng, n, 90, 1), with_w=False)
+    ioff, iidx, _ = oracle.csr_transpose(off, idx)
+    fwd = np.stack([oracle.bfs(off, idx, s) != INF for s in range(n)])
+    bwd = np.stack([oracle.bfs(ioff, iidx, v) != INF for v in range(n)])
+    assert (fwd == bwd.T).all()
+    lv = oracle.bfs(off, idx, 0)
+    # levels read through in-arcs: level(v) = 1 + min level over in-neighbours (Sec. 4.2)
+    for v in range(1, n):
+        ins = iidx[ioff[v]:ioff[v + 1]]
+        fin = [int(lv[u]) for u in ins if lv[u] != INF]
+        assert lv[v] == (min(fin) + 1 if fin else INF)
