@@ -332,6 +332,7 @@ def run_gpu(args):
         line["functors"] = bench_functors(llp, dev)
     if not args.no_batched:
         line["batched"] = bench_batched(llp, dev, stream)
+        line["batched_graphs"] = bench_batched_graphs(llp, dev)
     if not args.no_learned:
         line["learned"] = bench_learned(llp, dev, g, s)
     if rank == 0 and not args.no_cpu_baseline:
@@ -433,6 +434,56 @@ def bench_batched(llp, dev, stream):
             "plain_sample": "every 16th knapsack, 8th job DAG and 8th marriage instance, scaled",
             "cfg": {"threads": cfg.threads, "knap_unroll": cfg.knap_unroll}, "autotune_ms": tune_ms,
             "status": bst["status"], "cuda_graph": True}
+
+
+def bench_batched_graphs(llp, dev):
+    """Batched small SSSP/BFS (2,048 graphs of 64-8,192 vertices: uniform, power-law and grid
+    instances, every 4th a BFS) in one persistent launch replayed from a CUDA graph, against the
+    plain engine called once per graph (every 8th graph timed, scaled)."""
+    import torch
+    import synth
+    gb = synth.graph_batch()
+    db = llp.DeviceBatch(graphs=gb, device=dev)
+    ws = llp.workspace(llp.batch_workspace_size(db), dev)
+    st = torch.cuda.Stream(dev)
+    with torch.cuda.stream(st):
+        llp.batch_solve(db, ws=ws, stream=st)
+    st.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        llp.batch_solve(db, ws=ws, stream=st)
+    batched_ms = _ev_time(graph.replay, reps=5)
+    bst = llp.get_status(ws)
+    dist_b = db.t["gr_dist"].clone()
+    sidx = np.arange(0, gb["count"], 8)
+    gs = []
+    for i in sidx:
+        v0, v1 = int(gb["off"][i]), int(gb["off"][i + 1])
+        a, b = int(gb["arc_offsets"][v0]), int(gb["arc_offsets"][v1])
+        g = dict(n=v1 - v0, m=b - a, offsets=gb["arc_offsets"][v0:v1 + 1] - a, indices=gb["indices"][a:b],
+                 weights=gb["weights"][a:b])
+        gs.append((i, llp.DeviceGraph.from_host(g, dev), v0, v1))
+    nmax = int(np.diff(gb["off"]).max())
+    mmax = max(dg.m for _, dg, _, _ in gs)
+    wsp = llp.workspace(llp.sssp_workspace_size(nmax, mmax), dev)
+    outp = torch.empty(nmax, dtype=torch.int32, device=dev)
+
+    def plain():
+        for i, dg, _, _ in gs:
+            f = llp.bfs if gb["unit"][i] else llp.sssp
+            f(dg, int(gb["source"][i]), out=outp[:dg.n], ws=wsp)
+    plain_ms = _ev_time(plain, reps=1) * gb["count"] / len(sidx)
+    same = True
+    for i, dg, v0, v1 in gs[:16]:
+        f = llp.bfs if gb["unit"][i] else llp.sssp
+        f(dg, int(gb["source"][i]), out=outp[:dg.n], ws=wsp)
+        same &= bool(torch.equal(outp[:dg.n], dist_b[v0:v1]))
+    return {"metric": "instances/s", "instances": gb["count"], "vertices": int(gb["off"][-1]),
+            "arcs": int(gb["arc_offsets"][-1]), "batched_ms": batched_ms,
+            "batched_inst_per_s": gb["count"] / (batched_ms * 1e-3), "plain_ms_est": plain_ms,
+            "plain_inst_per_s": gb["count"] / (plain_ms * 1e-3), "speedup": plain_ms / batched_ms,
+            "plain_sample": "every 8th graph through llp_sssp / llp_bfs, scaled",
+            "batched_equals_plain_on_16": same, "status": bst["status"], "cuda_graph": True}
 
 
 def bench_functors(llp, dev):

@@ -260,7 +260,7 @@ llp_status_t llp_reduce(int64_t n, const uint64_t *x, uint64_t *sum, const llp_s
                         size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------- Batched
- * Many independent instances of three families solved in ONE persistent
+ * Many independent instances of four families solved in ONE persistent
  * launch (plus a one-CTA planning kernel): each CTA takes the next instance
  * from a device queue, most expensive first, and runs that instance's LLP
  * sweeps on its own (shared-memory state, CTA barriers).  Results are the same
@@ -298,6 +298,23 @@ typedef struct llp_batch {
     const int32_t *sm_men_pref;
     const int32_t *sm_women_rank;
     int32_t *sm_wife;
+    /* small SSSP / BFS (Sec. 4.1 / 4.2): graph i has vertices [gr_off[i], gr_off[i+1]) of the
+     * concatenated arrays; gr_arc_offsets (total_vertices + 1 entries) are positions in gr_indices /
+     * gr_weights, whose entries are LOCAL vertex ids of the same graph; gr_source[i] is local;
+     * gr_unit (may be NULL = every instance SSSP): gr_unit[i] != 0 makes instance i a BFS (levels,
+     * weights ignored); gr_weights may be NULL when every instance is a BFS.  gr_dist[total_vertices]
+     * receives distances / levels, 0xFFFFFFFF = unreachable; a finite path length >= 0xFFFFFFFF sets
+     * LLP_ERR_OVERFLOW.  The CTA keeps d[] and two frontier bitmaps in shared memory when
+     * 4.25 * n bytes fit, else it works on gr_dist in place. */
+    int32_t gr_count;
+    int32_t gr_max_n;
+    const int64_t *gr_off;         /* [gr_count + 1] */
+    const int64_t *gr_arc_offsets; /* [total_vertices + 1] */
+    const int32_t *gr_indices;
+    const uint32_t *gr_weights;
+    const int32_t *gr_source;      /* [gr_count] */
+    const int32_t *gr_unit;        /* [gr_count] or NULL */
+    uint32_t *gr_dist;             /* [total_vertices] out */
 } llp_batch_t;
 
 /* Launch shape of the batched engine (never changes results); 0 = default. */

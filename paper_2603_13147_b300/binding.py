@@ -382,7 +382,11 @@ class Batch(ctypes.Structure):
                 ("job_completion", ctypes.c_void_p),
                 ("sm_count", ctypes.c_int32), ("sm_max_n", ctypes.c_int32),
                 ("sm_n", ctypes.c_void_p), ("sm_pref_off", ctypes.c_void_p), ("sm_man_off", ctypes.c_void_p),
-                ("sm_men_pref", ctypes.c_void_p), ("sm_women_rank", ctypes.c_void_p), ("sm_wife", ctypes.c_void_p)]
+                ("sm_men_pref", ctypes.c_void_p), ("sm_women_rank", ctypes.c_void_p), ("sm_wife", ctypes.c_void_p),
+                ("gr_count", ctypes.c_int32), ("gr_max_n", ctypes.c_int32),
+                ("gr_off", ctypes.c_void_p), ("gr_arc_offsets", ctypes.c_void_p), ("gr_indices", ctypes.c_void_p),
+                ("gr_weights", ctypes.c_void_p), ("gr_source", ctypes.c_void_p), ("gr_unit", ctypes.c_void_p),
+                ("gr_dist", ctypes.c_void_p)]
 
 
 class BatchCfg(ctypes.Structure):
@@ -390,16 +394,16 @@ class BatchCfg(ctypes.Structure):
 
 
 class DeviceBatch:
-    """Device-resident batch of knapsack / job-DAG / stable-marriage instances
-    (host dicts as produced by synth.knapsack_batch / job_batch / marriage_batch)."""
+    """Device-resident batch of knapsack / job-DAG / stable-marriage / small SSSP-BFS instances
+    (host dicts as produced by synth.knapsack_batch / job_batch / marriage_batch / graph_batch)."""
 
-    def __init__(self, knap=None, job=None, sm=None, device="cuda"):
+    def __init__(self, knap=None, job=None, sm=None, graphs=None, device="cuda"):
         import numpy as np
         d = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(device)
         self.device = device
         self.t = {}
-        self.knap_count = self.job_count = self.sm_count = 0
-        self.knap_max_capacity = self.job_max_n = self.sm_max_n = 0
+        self.knap_count = self.job_count = self.sm_count = self.gr_count = 0
+        self.knap_max_capacity = self.job_max_n = self.sm_max_n = self.gr_max_n = 0
         if knap is not None and knap["count"] > 0:
             self.knap_count = int(knap["count"])
             self.knap_max_capacity = int(knap["capacity"].max())
@@ -423,19 +427,30 @@ class DeviceBatch:
                           sm_man_off=d(man_off, np.int64), sm_men_pref=d(sm["men_pref"], np.int32),
                           sm_women_rank=d(sm["women_rank"], np.int32),
                           sm_wife=torch.empty(int(man_off[-1]), dtype=torch.int32, device=device))
+        if graphs is not None and graphs["count"] > 0:
+            self.gr_count = int(graphs["count"])
+            self.gr_max_n = int(np.diff(graphs["off"]).max())
+            self.t.update(gr_off=d(graphs["off"], np.int64), gr_arc_offsets=d(graphs["arc_offsets"], np.int64),
+                          gr_indices=d(graphs["indices"], np.int32), gr_source=d(graphs["source"], np.int32),
+                          gr_dist=torch.empty(int(graphs["off"][-1]), dtype=torch.int32, device=device))
+            if graphs.get("weights") is not None:
+                self.t["gr_weights"] = d(np.asarray(graphs["weights"]).view(np.int32), np.int32)
+            if graphs.get("unit") is not None:
+                self.t["gr_unit"] = d(graphs["unit"], np.int32)
 
     def struct(self) -> Batch:
         b = Batch()
         b.knap_count, b.knap_max_capacity = self.knap_count, self.knap_max_capacity
         b.job_count, b.job_max_n = self.job_count, self.job_max_n
         b.sm_count, b.sm_max_n = self.sm_count, self.sm_max_n
+        b.gr_count, b.gr_max_n = self.gr_count, self.gr_max_n
         for k, v in self.t.items():
             setattr(b, k, v.data_ptr())
         return b
 
     @property
     def count(self):
-        return self.knap_count + self.job_count + self.sm_count
+        return self.knap_count + self.job_count + self.sm_count + self.gr_count
 
 
 def batch_workspace_size(db: DeviceBatch) -> int:

@@ -1,5 +1,5 @@
-// Batched LLP engine: thousands of uneven instances of three problem families
-// (0-1 knapsack, job scheduling, stable marriage) solved in ONE persistent
+// Batched LLP engine: thousands of uneven instances of four problem families
+// (0-1 knapsack, job scheduling, stable marriage, small SSSP/BFS) solved in ONE persistent
 // launch.  Each CTA repeatedly takes the next instance from a global queue and
 // solves it entirely on its own (the CTA-level solvers of problems.cuh: the
 // sweeps of one instance are separated by __syncthreads instead of grid
@@ -7,7 +7,7 @@
 //
 // The queue order is planned on the device by a one-CTA kernel: every instance
 // gets a cost estimate (knapsack: cells n*(W+1); jobs: arcs and jobs; marriage:
-// expected proposals n*ln n), and a counting sort on log2(cost) puts the most
+// expected proposals n*ln n; graphs: vertices and arcs), and a counting sort on log2(cost) puts the most
 // expensive first (longest-processing-time order), so the tail of the launch
 // is made of small instances.  The launch shape (threads per CTA, knapsack
 // register blocking) is picked by llp_batch_autotune, which times candidates.
@@ -21,7 +21,7 @@
 namespace llp {
 namespace {
 
-enum : uint32_t { kFamKnap = 0, kFamJob = 1, kFamSm = 2 };
+enum : uint32_t { kFamKnap = 0, kFamJob = 1, kFamSm = 2, kFamGraph = 3 };
 
 struct BatchArgs {
     llp_batch_t b;
@@ -63,10 +63,18 @@ __global__ void __launch_bounds__(1024) batch_plan_kernel(BatchArgs a) {
             return 64.0 * ((double)(j1 - j0) + m);
         }
         i -= b.job_count;
-        fam = kFamSm;
+        if (i < (uint32_t)b.sm_count) {
+            fam = kFamSm;
+            inst = i;
+            const double n = (double)b.sm_n[i];
+            return 256.0 * n * (log(n + 1.0) + 1.0);
+        }
+        i -= b.sm_count;
+        fam = kFamGraph;
         inst = i;
-        const double n = (double)b.sm_n[i];
-        return 256.0 * n * (log(n + 1.0) + 1.0);
+        const int64_t v0 = b.gr_off[i], v1 = b.gr_off[i + 1];
+        const double m = (double)(b.gr_arc_offsets[v1] - b.gr_arc_offsets[v0]);
+        return 128.0 * ((double)(v1 - v0) + m);
     };
     for (uint32_t i = threadIdx.x; i < a.total; i += blockDim.x) {
         uint32_t f, x;
@@ -145,6 +153,27 @@ __global__ void __launch_bounds__(1024, 1) batch_solve_kernel(BatchArgs a) {
             cells += (threadIdx.x == 0)
                          ? (unsigned long long)(b.job_succ_offsets[j0 + n] - b.job_succ_offsets[j0])
                          : 0ull;
+        } else if (fam == kFamGraph) {
+            const int64_t v0 = b.gr_off[i];
+            const int32_t n = (int32_t)(b.gr_off[i + 1] - v0);
+            const int32_t src = b.gr_source[i];
+            const bool unit = b.gr_unit && b.gr_unit[i];
+            if (n < 1 || n > b.gr_max_n || src < 0 || src >= n || (!unit && !b.gr_weights)) {
+                if (threadIdx.x == 0) set_status(h, LLP_ERR_INVALID_ARG);
+                continue;
+            }
+            const size_t nw = ((size_t)n + 31) / 32;
+            uint32_t *dout = b.gr_dist + v0;
+            const bool in_smem = (size_t)n * 4 + nw * 8 <= a.smem_bytes;
+            uint32_t *d = in_smem ? (uint32_t *)smem : dout;
+            uint32_t *bm = in_smem ? (uint32_t *)smem + n : (uint32_t *)gscratch;
+            unsigned long long arcs = 0;
+            graph_cta(n, b.gr_arc_offsets + v0, b.gr_indices, b.gr_weights, unit, src, d, bm, bm + nw, h, deadline,
+                      arcs);
+            if (in_smem)
+                for (int32_t v = threadIdx.x; v < n; v += blockDim.x) dout[v] = d[v];
+            cells += arcs;
+            __syncthreads();
         } else {
             const int32_t n = b.sm_n[i];
             if (n < 1 || n > b.sm_max_n) {
@@ -194,10 +223,14 @@ BatchPlan plan_batch(const llp_batch_t *b) {
         need = std::max(need, (size_t)(b->knap_max_capacity + 1) * 4);
     if (b->job_count > 0 && (size_t)b->job_max_n * 16 > p.smem_bytes) need = std::max(need, (size_t)b->job_max_n * 16);
     if (b->sm_count > 0 && (size_t)b->sm_max_n * 12 > p.smem_bytes) need = std::max(need, (size_t)b->sm_max_n * 12);
+    if (b->gr_count > 0) {
+        const size_t nw = ((size_t)b->gr_max_n + 31) / 32;
+        if ((size_t)b->gr_max_n * 4 + nw * 8 > p.smem_bytes) need = std::max(need, nw * 8);  // bitmaps only
+    }
     p.cta_scratch_bytes = align_up(need, 256);
     const DeviceInfo di = device_info();
     p.grid_max = (di.sms > 0 ? di.sms : 148);
-    const size_t total = (size_t)b->knap_count + b->job_count + b->sm_count;
+    const size_t total = (size_t)b->knap_count + b->job_count + b->sm_count + b->gr_count;
     Carve c(nullptr);
     c.take<uint32_t>(total);
     p.order_off = kHeaderBytes;
@@ -208,8 +241,8 @@ BatchPlan plan_batch(const llp_batch_t *b) {
 
 llp_status_t validate_batch(const llp_batch_t *b) {
     if (!b) return LLP_ERR_INVALID_ARG;
-    if (b->knap_count < 0 || b->job_count < 0 || b->sm_count < 0) return LLP_ERR_INVALID_ARG;
-    if ((int64_t)b->knap_count + b->job_count + b->sm_count > (1 << 29)) return LLP_ERR_INVALID_ARG;
+    if (b->knap_count < 0 || b->job_count < 0 || b->sm_count < 0 || b->gr_count < 0) return LLP_ERR_INVALID_ARG;
+    if ((int64_t)b->knap_count + b->job_count + b->sm_count + b->gr_count > (1 << 29)) return LLP_ERR_INVALID_ARG;
     if (b->knap_count > 0 && (!b->knap_item_off || !b->knap_w || !b->knap_v || !b->knap_capacity ||
                               !b->knap_best || b->knap_max_capacity < 0 || b->knap_max_capacity > (1 << 26)))
         return LLP_ERR_INVALID_ARG;
@@ -218,6 +251,9 @@ llp_status_t validate_batch(const llp_batch_t *b) {
         return LLP_ERR_INVALID_ARG;
     if (b->sm_count > 0 && (!b->sm_n || !b->sm_pref_off || !b->sm_man_off || !b->sm_men_pref ||
                             !b->sm_women_rank || !b->sm_wife || b->sm_max_n < 1 || b->sm_max_n > (1 << 24)))
+        return LLP_ERR_INVALID_ARG;
+    if (b->gr_count > 0 && (!b->gr_off || !b->gr_arc_offsets || !b->gr_source || !b->gr_dist || b->gr_max_n < 1 ||
+                            b->gr_max_n > (1 << 29)))
         return LLP_ERR_INVALID_ARG;
     return LLP_OK;
 }
@@ -258,7 +294,7 @@ llp_status_t llp_batch_solve(const llp_batch_t *b, const llp_batch_cfg_t *cfg, c
     BatchArgs a;
     a.b = *b;
     a.order = (uint32_t *)((char *)ws + p.order_off);
-    a.total = (uint32_t)((size_t)b->knap_count + b->job_count + b->sm_count);
+    a.total = (uint32_t)((size_t)b->knap_count + b->job_count + b->sm_count + b->gr_count);
     a.cta_scratch = (char *)ws + p.scratch_off;
     a.cta_scratch_bytes = p.cta_scratch_bytes;
     a.smem_bytes = p.smem_bytes;

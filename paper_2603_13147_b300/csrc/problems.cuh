@@ -285,6 +285,129 @@ __device__ __forceinline__ int32_t job_cta(int32_t n, const int64_t *off, const 
     return fixed;
 }
 
+// ------------------------------------------------------------ small SSSP / BFS
+// Paper Sec. 4.1 / 4.2 on one CTA.  d[] (n uint32, the state G) and the
+// frontier bitmaps cur/nxt (ceil(n/32) words each) are CTA-private: shared
+// memory, or global memory for large n (d may then be the output itself).
+// Sweep k expands the vertices whose bit is set in cur (advanced in sweep
+// k-1): warps take bitmap words in turn and expand a word's set vertices
+// together, their arcs balanced across the lanes; a candidate d(u) + w(u,v)
+// below d(v) makes v forbidden, the advance is an atomic min on d[v] and v's
+// bit is set in nxt.  A word of cur is cleared as it is read, so cur is empty
+// when it becomes nxt.  The CTA barrier ends a sweep; the run stops after a
+// sweep that advanced nothing.  off[] are the rows' arc positions in the
+// caller's concatenated arrays, idx[] local target ids.  Returns the number of
+// sweeps; arcs += arcs examined (per thread).
+__device__ __forceinline__ int32_t graph_cta(int32_t n, const int64_t *off, const int32_t *idx, const uint32_t *w,
+                                             bool unit, int32_t src, uint32_t *d, uint32_t *cur, uint32_t *nxt,
+                                             WsHeader *h, long long deadline, unsigned long long &arcs) {
+    constexpr int U = 4;  // arcs per lane in flight
+    __shared__ int s_more[3];
+    __shared__ int s_stop;
+    const int32_t nwords = (n + 31) >> 5;
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int32_t v = threadIdx.x; v < n; v += blockDim.x) d[v] = 0xFFFFFFFFu;
+    for (int32_t i = threadIdx.x; i < nwords; i += blockDim.x) {
+        cur[i] = 0u;
+        nxt[i] = 0u;
+    }
+    if (threadIdx.x == 0) {
+        s_more[0] = 1;
+        s_stop = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        d[src] = 0u;
+        cur[src >> 5] = 1u << (src & 31);
+    }
+    __syncthreads();
+    int32_t k = 0;
+    for (;;) {
+        k++;
+        if (threadIdx.x == 0) {
+            s_more[k % 3] = 0;
+            if (globaltimer_ns() > deadline) {
+                set_status(h, LLP_ERR_TIMEOUT);
+                s_stop = 1;
+            }
+        }
+        __syncthreads();
+        if (s_stop) break;
+        bool more = false;
+        for (int32_t wi = warp; wi < nwords; wi += nwarp) {
+            const uint32_t bits = *(volatile uint32_t *)&cur[wi];
+            if (bits == 0u) continue;
+            __syncwarp();
+            if (lane == 0) cur[wi] = 0u;
+            const bool own = lane < __popc(bits);
+            const int32_t u = own ? (wi << 5) + (int32_t)__fns(bits, 0, lane + 1) : 0;
+            uint32_t du = 0, deg = 0;
+            int64_t beg = 0;
+            if (own) {
+                du = *(volatile uint32_t *)&d[u];
+                beg = off[u];
+                deg = (uint32_t)(off[u + 1] - beg);
+            }
+            uint32_t incl = deg;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t excl = incl - deg;
+            arcs += (lane == 0) ? total : 0u;
+            for (uint32_t base = 0; base < total; base += 32 * U) {
+                int32_t v[U];
+                uint64_t cand[U];
+                bool ok[U];
+#pragma unroll
+                for (int j = 0; j < U; j++) {
+                    const uint32_t t = base + 32 * j + lane;
+                    int pos = 0;
+#pragma unroll
+                    for (int sh = 16; sh > 0; sh >>= 1) {
+                        const uint32_t probe = __shfl_sync(0xffffffffu, incl, pos + sh - 1);
+                        if (probe <= t) pos += sh;
+                    }
+                    ok[j] = t < total;
+                    const int owner = ok[j] ? pos : 0;
+                    const uint32_t ex = __shfl_sync(0xffffffffu, excl, owner);
+                    const int64_t bo = __shfl_sync(0xffffffffu, beg, owner);
+                    const uint32_t dq = __shfl_sync(0xffffffffu, du, owner);
+                    v[j] = 0;
+                    uint32_t wt = 0;
+                    if (ok[j]) {
+                        const int64_t e = bo + (int64_t)(t - ex);
+                        v[j] = __ldg(idx + e);
+                        wt = unit ? 1u : __ldg(w + e);
+                    }
+                    cand[j] = (uint64_t)dq + wt;
+                }
+#pragma unroll
+                for (int j = 0; j < U; j++) {
+                    if (!ok[j]) continue;
+                    if (cand[j] >= 0xFFFFFFFFull) {
+                        set_status(h, LLP_ERR_OVERFLOW);
+                        s_stop = 1;
+                    } else if ((uint32_t)cand[j] < *(volatile uint32_t *)&d[v[j]]) {
+                        atomicMin(&d[v[j]], (uint32_t)cand[j]);
+                        atomicOr(&nxt[v[j] >> 5], 1u << (v[j] & 31));
+                        more = true;
+                    }
+                }
+            }
+        }
+        if (more) s_more[k % 3] = 1;
+        __syncthreads();
+        if (!s_more[k % 3] || s_stop) break;
+        uint32_t *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    return k;
+}
+
 // ------------------------------------------------------- stable marriage CTA
 // Paper Sec. 4.3 on one CTA: best[] and next[] CTA-private (shared memory for
 // n <= a few thousand).  Threads take men in turn and carry displacement

@@ -223,3 +223,38 @@ def marriage_batch(count: int = 1024, nlo: int = 32, nhi: int = 1024, seed: int 
         a, b = marriage(int(ns[i]), seed * 1000003 + 7 * i + 1)
         mp[pref_off[i]:pref_off[i + 1]] = a.ravel(); wr[pref_off[i]:pref_off[i + 1]] = b.ravel()
     return dict(count=count, n=ns, pref_off=pref_off, men_pref=mp, women_rank=wr)
+
+
+def graph_batch(count: int = 2048, nlo: int = 64, nhi: int = 8192, seed: int = 5, bfs_every: int = 4):
+    """Batch of small graphs for batched SSSP/BFS, concatenated with local vertex ids.
+    Instance i is, by i mod 4: uniform (ER, n ~ U[nlo, nhi], 2-12 arcs per vertex, weights
+    U[1,255]), R-MAT (power law, scale from the drawn n, edge factor 8, weights U[1,255]),
+    a 4-neighbour grid (road-like, side from the drawn n, weights U[1,1000]), or uniform
+    again; sources: vertex 0, or the highest out-degree vertex for R-MAT.  Every bfs_every-th
+    instance is a BFS (unit = 1)."""
+    ns = sizes(count, nlo, nhi, seed, 401)
+    degs = sizes(count, 2, 12, seed, 402)
+    verts, arc_off, idxs, ws, srcs = [0], [], [], [], []
+    base = 0
+    for i in range(count):
+        n, s = int(ns[i]), seed * 1000003 + 11 * i + 3
+        kind = i % 4
+        if kind == 1:
+            g = rmat_graph(max(1, int(n).bit_length() - 1), 8, 0.57, 0.19, 0.19, 1, 255, seed=s)
+            src = max_out_degree_vertex(g)
+        elif kind == 2:
+            side = max(2, int(np.sqrt(n)))
+            g = grid_graph(side, side, 1, 1000, seed=s)
+            src = 0
+        else:
+            g = er_graph(n, n * int(degs[i]), 1, 255, seed=s)
+            src = 0
+        arc_off.append(g["offsets"][:-1] + base)
+        idxs.append(g["indices"]); ws.append(g["weights"]); srcs.append(src)
+        base += g["m"]
+        verts.append(verts[-1] + g["n"])
+    unit = np.array([1 if bfs_every and i % bfs_every == bfs_every - 1 else 0 for i in range(count)], np.int32)
+    return dict(count=count, off=np.array(verts, np.int64),
+                arc_offsets=np.concatenate(arc_off + [np.array([base], np.int64)]),
+                indices=np.concatenate(idxs), weights=np.concatenate(ws), source=np.array(srcs, np.int32),
+                unit=unit)
