@@ -145,6 +145,25 @@ size_t llp_sssp_workspace_size(int32_t n, int64_t m);
 llp_status_t llp_sssp(const llp_csr_t *g, int32_t source, uint32_t *dist, const llp_sched_t *sched,
                       void *ws, size_t ws_bytes, void *stream);
 
+/* Warm start (incremental re-solve).  Algorithm LLP (Sec. 3) reaches the same
+ * least solution from any state below it in the lattice order, so a previous
+ * result can be the starting state after the graph changed in a way that only
+ * shortens paths: arc weights decreased and/or arcs inserted (same n).  dist
+ * (in/out): on entry, for every v, a length of some path from `source` to v in
+ * the new graph, or 0xFFFFFFFF; the previous result of llp_sssp on the old
+ * graph is such a state.  seeds[0..n_seeds): every vertex with an out-arc that
+ * is new or whose weight decreased (duplicates allowed; vertices with an
+ * infinite distance are ignored): only their arcs can make an index forbidden
+ * in the entry state, so they are the initial_states_to_process of the run.
+ * On return dist holds the new shortest distances, bit-exact as llp_sssp on the
+ * new graph.  n_seeds = 0 returns dist unchanged (d[source] set to 0).  A seed
+ * outside [0, n) is skipped and sets LLP_ERR_INVALID_ARG (device status).
+ * If the entry state is not as stated (e.g. a finite value below a true
+ * distance) the result is the least fixed point above it, not the distances.
+ * Workspace: llp_sssp_workspace_size. */
+llp_status_t llp_sssp_warm(const llp_csr_t *g, int32_t source, uint32_t *dist, const int32_t *seeds,
+                           int32_t n_seeds, const llp_sched_t *sched, void *ws, size_t ws_bytes, void *stream);
+
 /* SSSP for callers that cannot allocate device memory.
  * Same computation and result as llp_sssp, but the scratch space comes from a
  * fixed 64 MiB array inside this library instead of a caller workspace, so the
@@ -177,6 +196,11 @@ llp_status_t llp_sssp_noalloc(const llp_csr_t *g, int32_t source, uint32_t *dist
 size_t llp_bfs_workspace_size(int32_t n, int64_t m);
 llp_status_t llp_bfs(const llp_csr_t *g, int32_t source, uint32_t *level, const llp_sched_t *sched,
                      void *ws, size_t ws_bytes, void *stream);
+
+/* BFS warm start after arc insertions: as llp_sssp_warm with unit weights
+ * (level in/out; seeds = sources of the inserted arcs).  Push sweeps only. */
+llp_status_t llp_bfs_warm(const llp_csr_t *g, int32_t source, uint32_t *level, const int32_t *seeds,
+                          int32_t n_seeds, const llp_sched_t *sched, void *ws, size_t ws_bytes, void *stream);
 
 /* BFS with direction switching.  Same result as llp_bfs; g_in is the
  * transpose of g (CSR of IN-arcs: row v lists the sources u of the arcs (u,v),

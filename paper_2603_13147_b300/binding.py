@@ -225,6 +225,38 @@ def bfs(g: DeviceGraph, source: int, out=None, sched: Sched | None = None, ws=No
     return _graph_call(lib().llp_bfs, bfs_workspace_size, g, source, out, sched, ws, stream, "llp_bfs")
 
 
+def _warm_call(fn, wsfn, g: DeviceGraph, source, dist, seeds, sched, ws, stream, what):
+    _dev(dist, torch.int32, "dist")
+    if seeds is not None and seeds.numel() > 0:
+        _dev(seeds, torch.int32, "seeds")
+    n_seeds = 0 if seeds is None else int(seeds.numel())
+    if ws is None:
+        ws = workspace(wsfn(g.n, g.m), g.indices.device)
+    c = g.csr()
+    rc = fn(ctypes.byref(c), ctypes.c_int32(source), _ptr(dist), _ptr(seeds) if n_seeds else None,
+            ctypes.c_int32(n_seeds), None if sched is None else ctypes.byref(sched), _ptr(ws),
+            ctypes.c_size_t(ws.numel()), _stream(stream))
+    _check(rc, what)
+    return dist, ws
+
+
+def sssp_warm(g: DeviceGraph, source: int, dist: torch.Tensor, seeds: torch.Tensor | None, sched=None, ws=None,
+              stream=None):
+    """Incremental SSSP (llp_sssp_warm): `dist` (in/out) holds upper bounds, e.g. the result on the
+    graph before weight decreases / arc insertions; `seeds` (int32) the tails of the changed arcs."""
+    if g.weights is None:
+        raise ValueError("sssp needs weights")
+    return _warm_call(lib().llp_sssp_warm, sssp_workspace_size, g, source, dist, seeds, sched, ws, stream,
+                      "llp_sssp_warm")
+
+
+def bfs_warm(g: DeviceGraph, source: int, level: torch.Tensor, seeds: torch.Tensor | None, sched=None, ws=None,
+             stream=None):
+    """Incremental BFS after arc insertions (llp_bfs_warm)."""
+    return _warm_call(lib().llp_bfs_warm, bfs_workspace_size, g, source, level, seeds, sched, ws, stream,
+                      "llp_bfs_warm")
+
+
 def bfs_pull(g: DeviceGraph, g_in: DeviceGraph, source: int, out=None, sched: Sched | None = None, ws=None,
              stream=None):
     """BFS with direction switching (llp_bfs_pull); g_in = g.transpose().  Returns (level, workspace)."""

@@ -101,6 +101,11 @@ struct GraphArgs {
     int32_t use_dev_sched;  // 1: take mode/delta/cfg from the header (learned scheduler)
     int32_t local_chain;    // batches per worklist item of the local chain, 0 = off
     long long deadline_ns;
+    // warm start: G starts from dist[] (upper bounds of the distances) and the first
+    // worklist is seeds[0..n_seeds) instead of the source alone
+    int32_t warm;
+    int32_t n_seeds;
+    const int32_t *seeds;
 };
 
 struct SweepCtx {
@@ -772,7 +777,9 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
             const int64_t v = base + 32 * q + lane_id();
             if (v < a.n) {
                 const unsigned long long cl = deg[q] == 0 ? 0ull : (deg[q] <= (uint32_t)c.small_max ? 1ull : 2ull);
-                a.key[v] = ((v == a.source) ? 0ull : ((unsigned long long)kInf << 32)) | cl;
+                const unsigned long long d0 =
+                    (v == a.source) ? 0ull : (a.warm ? (unsigned long long)a.dist[v] : (unsigned long long)kInf);
+                a.key[v] = (d0 << 32) | cl;
             }
             const uint32_t has = __ballot_sync(0xffffffffu, deg[q] > 0);
             const uint32_t large = __ballot_sync(0xffffffffu, deg[q] > (uint32_t)c.small_max);
@@ -790,12 +797,43 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
         h->mode_used = c.mode;
         h->delta_used = c.delta;
         h->block_cfg_used = c.cfg;
-        h->scratch[8] = (uint32_t)c.chain;
         for (int i = 0; i < 3; i++) h->far_min[i] = kInf;
         h->list_ok[1] = 1;
     }
     bool alive = grid_barrier(h, phase, deadline);
-    if (gtid == 0 && alive) {
+    c.st_small = s_stage_small[threadIdx.x >> 5];
+    c.st_chunk = s_stage_chunk[threadIdx.x >> 5];
+    c.lq = s_lq[threadIdx.x >> 5];
+    if (a.warm && alive) {
+        // initial_states_to_process of a warm start: every seed with a finite d and
+        // out-arcs enters B_1 (deduplicated) and the worklists of sweep 1
+        c.k = 0;
+        c.bm_next = a.bm[1];
+        for (int64_t base = gwarp * 32; base < a.n_seeds; base += nwarps * 32) {
+            const int64_t i = base + lane_id();
+            int32_t u = i < a.n_seeds ? a.seeds[i] : -1;
+            if (i < a.n_seeds && (uint32_t)u >= (uint32_t)a.n) {
+                set_status(h, LLP_ERR_INVALID_ARG);
+                u = -1;
+            }
+            uint32_t cl = 0;
+            bool nw = false;
+            if (u >= 0) {
+                const unsigned long long kv = __ldcg(a.key + u);
+                cl = (uint32_t)kv & 3u;
+                if (cl != 0 && key_dist(kv) != kInf) {
+                    const uint32_t bit = 1u << (u & 31);
+                    nw = (atomicOr(a.bm[1] + (u >> 5), bit) & bit) == 0;
+                }
+            }
+            const bool nw1[1] = {nw};
+            const int32_t u1[1] = {u < 0 ? 0 : u};
+            const uint32_t c1[1] = {cl};
+            append_new(a, nw1, u1, c1, c);
+        }
+        flush_sweep(a, c, &s_flush);
+    }
+    if (gtid == 0 && alive && !a.warm) {
         const uint32_t src_deg = (uint32_t)(__ldg(a.off + a.source + 1) - __ldg(a.off + a.source));
         if (src_deg > 0) {
             a.bm[1][a.source >> 5] = 1u << (a.source & 31);
@@ -811,11 +849,9 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
     }
     if (alive) alive = grid_barrier(h, phase, deadline);
 
-    c.st_small = s_stage_small[threadIdx.x >> 5];
-    c.st_chunk = s_stage_chunk[threadIdx.x >> 5];
-    c.lq = s_lq[threadIdx.x >> 5];
     c.chain = a.local_chain;
     if (a.use_dev_sched && *(volatile int32_t *)&h->sched_valid) c.chain = *(volatile int32_t *)&h->sched_chain;
+    if (gtid == 0) h->scratch[8] = (uint32_t)c.chain;
     c.k = 1;
     c.fa = 0;
     c.bucket_hi = (c.delta == kInf) ? (1ull << 40) : (unsigned long long)c.delta;
@@ -1035,8 +1071,10 @@ void resolve_schedule(const llp_sched_t *s, bool unit, int32_t n, int64_t m, int
 
 template <bool UNIT>
 llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, const llp_sched_t *s, void *ws,
-                         size_t ws_bytes, cudaStream_t stream, const llp_csr_t *gin = nullptr) {
+                         size_t ws_bytes, cudaStream_t stream, const llp_csr_t *gin = nullptr,
+                         const int32_t *seeds = nullptr, int32_t n_seeds = -1) {
     if (!g || !out || !ws) return LLP_ERR_INVALID_ARG;
+    if (n_seeds > 0 && !seeds) return LLP_ERR_INVALID_ARG;
     if (gin && (gin->n != g->n || gin->m != g->m || gin->offsets_64 != g->offsets_64 || !gin->offsets ||
                 (gin->m > 0 && !gin->indices)))
         return LLP_ERR_INVALID_ARG;
@@ -1098,6 +1136,9 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         args.use_dev_sched = learned ? 1 : 0;
         args.local_chain = (s && s->local_chain > 0) ? s->local_chain : 0;
         args.deadline_ns = deadline_from(s);
+        args.warm = n_seeds >= 0 ? 1 : 0;
+        args.n_seeds = n_seeds > 0 ? n_seeds : 0;
+        args.seeds = seeds;
     };
     if (g->offsets_64) {
         GraphArgs<int64_t> args;
@@ -1195,6 +1236,20 @@ llp_status_t llp_sssp(const llp_csr_t *g, int32_t source, uint32_t *dist, const 
 llp_status_t llp_bfs(const llp_csr_t *g, int32_t source, uint32_t *level, const llp_sched_t *sched, void *ws,
                      size_t ws_bytes, void *stream) {
     return llp::graph_solve<true>(g, source, level, sched, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+llp_status_t llp_sssp_warm(const llp_csr_t *g, int32_t source, uint32_t *dist, const int32_t *seeds, int32_t n_seeds,
+                           const llp_sched_t *sched, void *ws, size_t ws_bytes, void *stream) {
+    if (n_seeds < 0) return LLP_ERR_INVALID_ARG;
+    return llp::graph_solve<false>(g, source, dist, sched, ws, ws_bytes, (cudaStream_t)stream, nullptr, seeds,
+                                   n_seeds);
+}
+
+llp_status_t llp_bfs_warm(const llp_csr_t *g, int32_t source, uint32_t *level, const int32_t *seeds, int32_t n_seeds,
+                          const llp_sched_t *sched, void *ws, size_t ws_bytes, void *stream) {
+    if (n_seeds < 0) return LLP_ERR_INVALID_ARG;
+    return llp::graph_solve<true>(g, source, level, sched, ws, ws_bytes, (cudaStream_t)stream, nullptr, seeds,
+                                  n_seeds);
 }
 
 llp_status_t llp_bfs_pull(const llp_csr_t *g, const llp_csr_t *g_in, int32_t source, uint32_t *level,

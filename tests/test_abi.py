@@ -101,3 +101,19 @@ def test_pull_and_transpose_arguments_rejected_on_host(L):
     c.m = 5  # arcs but no indices
     assert L.llp_csr_transpose(ctypes.byref(c), out, ctypes.c_void_p(0x300000), None, ws, big,
                                None) == llp.LLP_ERR_INVALID_ARG
+
+
+def test_warm_arguments_rejected_on_host(L):
+    import paper_2603_13147_b300 as llp
+    c = llp.Csr()
+    c.n, c.m = 10, 0
+    c.offsets = 0x1000
+    ws = ctypes.c_void_p(0x100000)
+    out = ctypes.c_void_p(0x200000)
+    big = ctypes.c_size_t(1 << 30)
+    for f in (L.llp_sssp_warm, L.llp_bfs_warm):
+        assert f(ctypes.byref(c), 0, out, None, -1, None, ws, big, None) == llp.LLP_ERR_INVALID_ARG
+        assert f(ctypes.byref(c), 0, out, None, 3, None, ws, big, None) == llp.LLP_ERR_INVALID_ARG
+        assert f(ctypes.byref(c), 10, out, None, 0, None, ws, big, None) == llp.LLP_ERR_INVALID_ARG
+        assert f(ctypes.byref(c), 0, out, None, 0, None, ws, ctypes.c_size_t(64), None) == \
+            llp.LLP_ERR_WORKSPACE_TOO_SMALL

@@ -349,3 +349,99 @@ def test_rmat22_bfs_pull_full(llp, rmat22):
     assert st["pull_sweeps"] >= 1
     d64, _ = run_bfs_pull(llp, g, s, offsets_64=True)
     assert (d64 == ref).all()
+
+
+# ------------------------------------------------- warm start (incremental re-solve)
+
+def shorten(g, rng, frac_dec, n_ins, wmax=100):
+    """Decrease a random fraction of the weights and insert random arcs.  Returns the new graph
+    (CSR, arcs sorted by tail) and the tails of every changed or inserted arc."""
+    n = g["n"]
+    src = np.repeat(np.arange(n, dtype=np.int32), np.diff(g["offsets"]))
+    dst = g["indices"].copy()
+    w = g["weights"].copy()
+    dec = rng.random(len(w)) < frac_dec
+    w[dec] = np.maximum(1, w[dec] // 3)
+    ins_s = rng.integers(0, n, n_ins).astype(np.int32)
+    ins_d = rng.integers(0, n, n_ins).astype(np.int32)
+    ins_w = rng.integers(1, wmax + 1, n_ins).astype(np.uint32)
+    src = np.concatenate([src, ins_s]); dst = np.concatenate([dst, ins_d]); w = np.concatenate([w, ins_w])
+    order = np.argsort(src, kind="stable")
+    off = np.zeros(n + 1, np.int64)
+    np.add.at(off, src + 1, 1)
+    gn = dict(n=n, m=len(dst), offsets=np.cumsum(off), indices=dst[order], weights=w[order])
+    seeds = np.unique(np.concatenate([src[:len(dec)][dec], ins_s])).astype(np.int32)
+    return gn, seeds
+
+
+def run_warm(llp, g, s, d_old, seeds, unit=False, **kw):
+    dg = dev_graph(llp, g, kw.pop("offsets_64", False))
+    sched = llp.make_sched(**kw) if kw else None
+    dist = torch.from_numpy(d_old.view(np.int32).copy()).cuda()
+    sd = torch.from_numpy(seeds).cuda() if seeds is not None and len(seeds) else None
+    f = llp.bfs_warm if unit else llp.sssp_warm
+    d, ws = f(dg, s, dist, sd, sched=sched)
+    st = llp.get_status(ws)
+    assert st["status"] == 0, st
+    return llp.as_u32(d), st
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(mode=1, delta=64), dict(mode=2), dict(mode=1, local_chain=16),
+                                dict(delta=300, block_cfg=3, threads=256)])
+def test_warm_er16k(llp, kw):
+    g = synth.er16k()
+    rng = np.random.default_rng(31)
+    d_old = oracle.sssp(g["offsets"], g["indices"], g["weights"], 0)
+    gn, seeds = shorten(g, rng, 0.02, 300)
+    d, st = run_warm(llp, gn, 0, d_old, seeds, **kw)
+    assert (d == oracle.sssp(gn["offsets"], gn["indices"], gn["weights"], 0)).all()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_warm_random_graphs(llp, seed):
+    rng = np.random.default_rng(800 + seed)
+    n = int(rng.integers(2, 4000))
+    arcs = [(int(rng.integers(n)), int(rng.integers(n)), int(rng.integers(1, 1000)))
+            for _ in range(int(rng.integers(0, 5 * n)))]
+    arcs += [(0, int(rng.integers(n)), int(rng.integers(1, 50))) for _ in range(int(rng.integers(0, 800)))]
+    g = csr_from_arcs(n, arcs)
+    s = int(rng.integers(n))
+    d_old = oracle.sssp(g["offsets"], g["indices"], g["weights"], s)
+    gn, seeds = shorten(g, rng, float(rng.random()) * 0.2, int(rng.integers(0, n)), 1000)
+    ref = oracle.sssp(gn["offsets"], gn["indices"], gn["weights"], s)
+    d, _ = run_warm(llp, gn, s, d_old, seeds, offsets_64=bool(seed % 2))
+    assert (d == ref).all()
+    # BFS after the same insertions (levels only shrink)
+    lv_old = oracle.bfs(g["offsets"], g["indices"], s)
+    lv, _ = run_warm(llp, gn, s, lv_old, seeds, unit=True)
+    assert (lv == oracle.bfs(gn["offsets"], gn["indices"], s)).all()
+
+
+def test_warm_grid_and_rmat(llp):
+    for g, s in ((synth.grid_graph(64, 80, 1, 1000, seed=3), 0), (synth.rmat(16, seed=21), None)):
+        s = synth.max_out_degree_vertex(g) if s is None else s
+        rng = np.random.default_rng(5)
+        d_old = oracle.sssp(g["offsets"], g["indices"], g["weights"], s)
+        gn, seeds = shorten(g, rng, 0.01, 50, 255)
+        d, _ = run_warm(llp, gn, s, d_old, seeds)
+        assert (d == oracle.sssp(gn["offsets"], gn["indices"], gn["weights"], s)).all()
+
+
+def test_warm_without_changes_and_from_scratch_state(llp):
+    g = synth.er16k()
+    ref = oracle.sssp(g["offsets"], g["indices"], g["weights"], 0)
+    d, st = run_warm(llp, g, 0, ref, None)  # nothing changed: the state is already the fixed point
+    assert (d == ref).all() and st["advances"] == 0
+    # the bottom state with the source as the only seed is the cold start
+    bottom = np.full(g["n"], oracle.INF, np.uint32)
+    d, _ = run_warm(llp, g, 0, bottom, np.array([0], np.int32))
+    assert (d == ref).all()
+
+
+def test_warm_invalid_seed_reported(llp):
+    g = synth.er16k()
+    ref = oracle.sssp(g["offsets"], g["indices"], g["weights"], 0)
+    dg = dev_graph(llp, g)
+    dist = torch.from_numpy(ref.view(np.int32).copy()).cuda()
+    _, ws = llp.sssp_warm(dg, 0, dist, torch.tensor([3, g["n"]], dtype=torch.int32, device="cuda"))
+    assert llp.get_status(ws)["status"] == llp.LLP_ERR_INVALID_ARG
