@@ -338,14 +338,20 @@ __device__ __forceinline__ void relax_multi(const GraphArgs<OffT> &a, const bool
 
 // Expand the out-arcs of up to 32 small vertices (one per lane) edge-balanced
 // across the warp, kUnroll batches of 32 arcs at a time.
+// skip (may be NULL): a lane whose vertex has its bit set there is dropped (the
+// word is loaded together with the vertex's distance and row bounds).
 template <typename OffT, bool UNIT>
-__device__ __forceinline__ void expand_group(const GraphArgs<OffT> &a, bool valid, int32_t u, SweepCtx &c) {
+__device__ __forceinline__ void expand_group(const GraphArgs<OffT> &a, bool valid, int32_t u, SweepCtx &c,
+                                             const uint32_t *skip = nullptr) {
     uint32_t du = 0, deg = 0;
     OffT beg = 0;
     if (valid) {
+        const uint32_t sk = skip ? __ldcg(skip + (u >> 5)) : 0u;
         du = key_dist(__ldcg(a.key + u));
         beg = __ldg(a.off + u);
-        deg = (uint32_t)(__ldg(a.off + u + 1) - beg);
+        const OffT end = __ldg(a.off + u + 1);
+        valid = ((sk >> (u & 31)) & 1u) == 0;
+        deg = valid ? (uint32_t)(end - beg) : 0u;
     }
     c.items += valid;
     uint32_t incl = deg;
@@ -426,16 +432,19 @@ __device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item
     const int32_t u = item.x;
     const uint32_t bit = 1u << (u & 31);
     uint32_t nxt = 0, du = 0;
+    OffT b0 = 0, e0 = 0;
     if (lane_id() == 0) {
         nxt = __ldcg(c.bm_next + (u >> 5));
         du = key_dist(__ldcg(a.key + u));
+        b0 = __ldg(a.off + u);
+        e0 = __ldg(a.off + u + 1);
         if (item.y == 0) red_and(c.bm_cur + (u >> 5), ~bit);
     }
     nxt = __shfl_sync(0xffffffffu, nxt, 0);
-    du = __shfl_sync(0xffffffffu, du, 0);
     if (nxt & bit) return;  // advanced again meanwhile: sweep k+1 handles it (warp-uniform)
-    const OffT b0 = __ldg(a.off + u);
-    const OffT e0 = __ldg(a.off + u + 1);
+    du = __shfl_sync(0xffffffffu, du, 0);
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    e0 = __shfl_sync(0xffffffffu, e0, 0);
     const OffT beg = b0 + (OffT)item.y * (OffT)c.chunk_edges;
     const OffT end = min(e0, beg + (OffT)c.chunk_edges);
     c.items += (lane_id() == 0 && item.y == 0);
@@ -471,9 +480,11 @@ __device__ __forceinline__ void scan_words(const GraphArgs<OffT> &a, int64_t g, 
     uint32_t act = 0;
     if (lane_id() < kGroupWords && wi < a.nwords) {
         const uint32_t b = __ldcg(c.bm_cur + wi);
+        const uint32_t large = __ldg(&a.cls[wi].y);
+        const uint32_t again = __ldcg(c.bm_next + wi);
         if (b) {
             c.bm_cur[wi] = 0u;
-            act = b & ~__ldg(&a.cls[wi].y) & ~__ldcg(c.bm_next + wi);
+            act = b & ~large & ~again;
         }
     }
     const uint32_t cnt = __popc(act);
@@ -726,6 +737,7 @@ template <typename OffT, bool UNIT, bool PULL>
 __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) {
     __shared__ BlockFlush s_flush;
     __shared__ uint32_t s_work[2];
+    __shared__ uint32_t s_cwork[2];
     __shared__ int32_t s_stage_small[16][kStageSmall];
     __shared__ int2 s_stage_chunk[16][kStageChunk];
     __shared__ int32_t s_lq[16][kLocalQ];
@@ -743,6 +755,8 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
         s_flush.edges = 0;
         s_work[0] = 0;
         s_work[1] = 0;
+        s_cwork[0] = 0;
+        s_cwork[1] = 0;
     }
 
     SweepCtx c;
@@ -875,7 +889,10 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
         if (ns + nc == 0) c.dense_next = false;
         c.pull = PULL && UNIT && c.chain == 0 && ns + nc > 0 && arcs > a.pull_arcs;
         if (c.pull) c.dense_next = false;  // a pull sweep appends every vertex it reaches
-        if (threadIdx.x == 0) s_work[(k + 1) & 1] = 0;  // used after the next grid barrier
+        if (threadIdx.x == 0) {  // used after the next grid barrier
+            s_work[(k + 1) & 1] = 0;
+            s_cwork[(k + 1) & 1] = 0;
+        }
         if (gtid == 0) {
             const uint32_t r = (k + 2) % 3;
             h->n_small[r] = 0;
@@ -949,10 +966,17 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
             }
         } else {
             dense_sweeps += dense;
-            // chunks: static round robin (uniform cost, <= chunk_edges arcs)
+            // chunks: CTA b owns items b, b + G, b + 2G, ... (G = grid size; a hub's chunks
+            // are consecutive in the list, so they spread over CTAs) and its warps take them
+            // in turn from a shared counter (costs vary: skipped, partial and full chunks)
             const int2 *cl = a.chunk[k & 1];
             c.chain_on = c.chain > 0;
-            for (int64_t it = gwarp; it < nc; it += nwarps) {
+            for (;;) {
+                uint32_t j = 0;
+                if (lane_id() == 0) j = atomicAdd(&s_cwork[k & 1], 1u);
+                j = __shfl_sync(0xffffffffu, j, 0);
+                const uint64_t it = (uint64_t)blockIdx.x + (uint64_t)j * gridDim.x;
+                if (it >= nc) break;
                 expand_chunk<OffT, UNIT>(a, cl[it], c);
                 if (c.chain_on) drain_local<OffT, UNIT>(a, c);
             }
@@ -975,12 +999,8 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
                     const int64_t i = (int64_t)g * 32 + lane_id();
                     bool ok = i < ns;
                     int32_t u = ok ? sl[i] : 0;
-                    if (ok) {
-                        const uint32_t bit = 1u << (u & 31);
-                        red_and(c.bm_cur + (u >> 5), ~bit);
-                        ok = (__ldcg(c.bm_next + (u >> 5)) & bit) == 0;
-                    }
-                    expand_group<OffT, UNIT>(a, ok, u, c);
+                    if (ok) red_and(c.bm_cur + (u >> 5), ~(1u << (u & 31)));
+                    expand_group<OffT, UNIT>(a, ok, u, c, c.bm_next);  // advanced again: next sweep
                     if (c.chain_on) drain_local<OffT, UNIT>(a, c);
                 }
             }
