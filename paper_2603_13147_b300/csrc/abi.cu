@@ -84,7 +84,7 @@ llp_status_t llp_get_status(const void *ws, void *stream, llp_stats_t *out) {
     out->block_cfg_used = h.block_cfg_used;
     out->dense_sweeps = h.dense_sweeps;
     out->local_chain_used = (int32_t)h.scratch[8];
-    out->pull_sweeps = (int32_t)h.scratch[9];
+    out->pull_sweeps = (int32_t)h.scratch[7];
     return h.status;
 }
 

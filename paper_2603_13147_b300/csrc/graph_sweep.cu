@@ -1027,7 +1027,7 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
     if (gtid == 0) {
         h->sweeps = (int32_t)c.k;
         h->dense_sweeps = (int32_t)dense_sweeps;
-        h->scratch[9] = pull_sweeps;
+        h->scratch[7] = pull_sweeps;
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -56,6 +56,8 @@ struct alignas(256) WsHeader {
     uint32_t far_min[3];
     uint32_t list_ok[3];
     unsigned long long sweep_edges[2];
+    // [0] CTAs finished (t_end), [1..2] closure change flags, [7] pull sweeps,
+    // [8] local chain used, [9..14] feature accumulators, [15] feature CTAs finished
     uint32_t scratch[16];
     // ---- schedule chosen on the device by the learned scheduler (graph engine)
     int32_t sched_mode;

@@ -83,12 +83,24 @@ __global__ void __launch_bounds__(kFeatThreads) graph_features_kernel(int32_t n,
         ws += (float)x;
         wq += (float)x * (float)x;
     }
-    atomicAdd(&s_deg, dsum);
-    atomicMax(&s_maxdeg, dmax);
-    atomicMin(&s_wmin, wmn);
-    atomicMax(&s_wmax, wmx);
-    atomicAdd(&s_wsum, ws);
-    atomicAdd(&s_wsq, wq);
+    // warp reductions first: one shared-memory atomic per warp and quantity
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+        dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        wmn = min(wmn, __shfl_xor_sync(0xffffffffu, wmn, o));
+        wmx = max(wmx, __shfl_xor_sync(0xffffffffu, wmx, o));
+        ws += __shfl_xor_sync(0xffffffffu, ws, o);
+        wq += __shfl_xor_sync(0xffffffffu, wq, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s_deg, dsum);
+        atomicMax(&s_maxdeg, dmax);
+        atomicMin(&s_wmin, wmn);
+        atomicMax(&s_wmax, wmx);
+        atomicAdd(&s_wsum, ws);
+        atomicAdd(&s_wsq, wq);
+    }
     __syncthreads();
     // header accumulators: scratch[9..14] (zeroed with the header)
     uint32_t *acc = h->scratch + 9;
@@ -143,11 +155,36 @@ __device__ __forceinline__ int argmax_head(const float *z, int lo, int len) {
 }
 
 // One CTA (>= max(H1, H2, O) threads): MLP on h->feat, then the schedule.
+// The parameters are first copied to shared memory with independent loads
+// (the layer loops then read shared memory instead of waiting on one global
+// load per step); networks larger than the buffer read them in place.
+constexpr int kSchedSmemParams = 8192;
+constexpr int kSchedThreads = 256;  // >= kMaxDim; all threads copy the parameters
 __global__ void mlp_schedule_kernel(const float *params, MlpDims d, WsHeader *h) {
     __shared__ float x[kMaxDim], h1[kMaxDim], h2[kMaxDim], z[kMaxDim];
-    const float *W1 = params, *b1 = W1 + d.F * d.H1, *W2 = b1 + d.H1, *b2 = W2 + d.H1 * d.H2, *W3 = b2 + d.H2,
-                *b3 = W3 + d.H2 * d.O;
+    __shared__ float sp[kSchedSmemParams];
     const int t = threadIdx.x;
+    const int np = (int)mlp_param_count(d);
+    const float *P = params;
+    if (np <= kSchedSmemParams) {
+        constexpr int U = 8;  // independent loads in flight per thread
+        for (int i0 = t; i0 < np; i0 += U * blockDim.x) {
+            float r[U];
+#pragma unroll
+            for (int j = 0; j < U; j++) {
+                const int i = i0 + j * blockDim.x;
+                r[j] = i < np ? __ldg(params + i) : 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < U; j++) {
+                const int i = i0 + j * blockDim.x;
+                if (i < np) sp[i] = r[j];
+            }
+        }
+        P = sp;
+    }
+    const float *W1 = P, *b1 = W1 + d.F * d.H1, *W2 = b1 + d.H1, *b2 = W2 + d.H1 * d.H2, *W3 = b2 + d.H2,
+                *b3 = W3 + d.H2 * d.O;
     if (t < d.F) x[t] = h->feat[t];
     __syncthreads();
     if (t < d.H1) {
@@ -365,7 +402,7 @@ llp_status_t enqueue_learned_schedule(const llp_csr_t *g, int32_t source, bool u
     else
         graph_features_kernel<int32_t><<<kFeatBlocks, kFeatThreads, 0, st>>>(g->n, g->m, (const int32_t *)g->offsets,
                                                                               w, source, h);
-    mlp_schedule_kernel<<<1, block_for(d), 0, st>>>(params, d, h);
+    mlp_schedule_kernel<<<1, kSchedThreads, 0, st>>>(params, d, h);
     LLP_CUDA_TRY(cudaGetLastError());
     return LLP_OK;
 }
