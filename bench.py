@@ -401,16 +401,32 @@ def _ev_time(fn, reps=3, stream=None):
     return float(np.median(ts))
 
 
-def bench_batched(llp, dev, stream):
+def smem_peak_gbs(dev):
+    """Shared-memory bandwidth of the GPU: 128 B per clock per SM at the maximum SM clock."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    mhz = 2032.0
+    try:
+        import pynvml
+        pynvml.nvmlInit()
+        h = pynvml.nvmlDeviceGetHandleByIndex(dev.index if dev.index is not None else 0)
+        mhz = float(pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM))
+    except Exception:
+        pass
+    return props.multi_processor_count * 128.0 * mhz * 1e6 / 1e9, mhz
+
+
+def bench_batched(llp, dev, stream, div=1):
     """Batched workload (4,096 knapsack + 2,048 job DAGs + 1,024 stable marriages): one
     persistent launch, autotuned launch shape, replayed from a CUDA graph, against the
     plain engine called once per instance on the same stream (timed on a sample of
-    every family and scaled to the full counts)."""
+    every family and scaled to the full counts).  The knapsack family alone is timed
+    too, for its shared-memory roofline.  div > 1 shrinks every family (profiling)."""
     import torch
     import synth
-    knap = synth.knapsack_batch()
-    job = synth.job_batch()
-    sm = synth.marriage_batch()
+    knap = synth.knapsack_batch(4096 // div)
+    job = synth.job_batch(2048 // div)
+    sm = synth.marriage_batch(1024 // div)
     db = llp.DeviceBatch(knap, job, sm, device=dev)
     ws = llp.workspace(llp.batch_workspace_size(db), dev)
     cfg, tune_ms, ws = llp.batch_autotune(db, ws=ws, stream=stream)
@@ -424,6 +440,20 @@ def bench_batched(llp, dev, stream):
     batched_ms = _ev_time(graph.replay, reps=3)
     bst = llp.get_status(ws)
     total = db.count
+
+    # knapsack family alone: 3 shared-memory accesses of 4 B per cell (two reads of the previous
+    # row, one write), Sigma n_i (W_i + 1) cells
+    dk = llp.DeviceBatch(knap, None, None, device=dev)
+    wsk_b = llp.workspace(llp.batch_workspace_size(dk), dev)
+    knap_ms = _ev_time(lambda: llp.batch_solve(dk, cfg, ws=wsk_b, stream=stream), reps=3, stream=stream)
+    cells = int(np.sum(np.diff(knap["item_off"]) * (knap["capacity"].astype(np.int64) + 1)))
+    peak_smem, sm_mhz = smem_peak_gbs(dev)
+    ach = 12.0 * cells / (knap_ms * 1e-3) / 1e9
+    knap_roof = {"bound": "smem", "achieved": ach, "peak": peak_smem, "unit": "GB/s", "frac": ach / peak_smem,
+                 "cells": cells, "ms": knap_ms, "cells_per_s": cells / (knap_ms * 1e-3),
+                 "peak_note": f"SMs x 128 B/clk x {sm_mhz:.0f} MHz (nominal shared-memory bandwidth)",
+                 "alg_bytes_per_cell": 12}
+    del dk, wsk_b
 
     # plain engine: one single-instance call per instance (sampled per family)
     wk = torch.from_numpy(knap["w"]).to(dev)
@@ -470,7 +500,7 @@ def bench_batched(llp, dev, stream):
             "plain_family_ms_est": {"knapsack": t_knap, "job": t_job, "marriage": t_sm},
             "plain_sample": "every 16th knapsack, 8th job DAG and 8th marriage instance, scaled",
             "cfg": {"threads": cfg.threads, "knap_unroll": cfg.knap_unroll}, "autotune_ms": tune_ms,
-            "status": bst["status"], "cuda_graph": True}
+            "status": bst["status"], "cuda_graph": True, "knapsack_roofline": knap_roof}
 
 
 def bench_batched_graphs(llp, dev):
@@ -638,7 +668,17 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-scheduler stream section")
     ap.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (22 = the benchmarked workload; "
                     "smaller scales are for profiling captures)")
+    ap.add_argument("--batched-only", type=int, default=0, metavar="DIV",
+                    help="profiling: run only the batched section with every family divided by DIV, "
+                         "print its JSON and exit (not a benchmark line)")
     args = ap.parse_args()
+    if args.batched_only:
+        import torch
+        import paper_2603_13147_b300 as llp
+        dev = torch.device("cuda", 0)
+        llp.lib()
+        print(json.dumps(bench_batched(llp, dev, torch.cuda.current_stream(dev), div=args.batched_only)))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
