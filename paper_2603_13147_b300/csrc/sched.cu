@@ -211,8 +211,8 @@ __global__ void mlp_schedule_kernel(const float *params, MlpDims d, WsHeader *h)
         const int cfg = argmax_head(z, d.heads[0] + d.heads[1], d.heads[2]);
         h->sched_mode = mode;  // LLP_MODE_AUTO / SPARSE / DENSE
         uint32_t delta = kInf;
-        if (dc > 0) {          // class c >= 1: width = wmax * 2^(c-3), at least 1
-            const float wd = ldexpf(h->feat_wmax, dc - 3);
+        if (dc > 0) {          // class c >= 1: width = wmax * 2^(c-1), at least 1
+            const float wd = ldexpf(h->feat_wmax, dc - 1);
             delta = wd < 1.f ? 1u : (wd > 2147483647.f ? 2147483647u : (uint32_t)wd);
         }
         h->sched_delta = delta;

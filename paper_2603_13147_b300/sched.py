@@ -40,7 +40,7 @@ def delta_of_class(c: int, wmax: int) -> int:
     """Bucket width of class c (0 = no buckets), as the inference kernel maps it."""
     if c == 0:
         return B.DELTA_INF
-    wd = float(np.float32(wmax)) * 2.0 ** (c - 3)
+    wd = float(np.float32(wmax)) * 2.0 ** (c - 1)
     return 1 if wd < 1.0 else int(min(wd, 2147483647.0))
 
 
