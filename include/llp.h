@@ -145,6 +145,19 @@ size_t llp_sssp_workspace_size(int32_t n, int64_t m);
 llp_status_t llp_sssp(const llp_csr_t *g, int32_t source, uint32_t *dist, const llp_sched_t *sched,
                       void *ws, size_t ws_bytes, void *stream);
 
+/* SSSP on a graph in HOST memory: h_g's offsets/indices/weights and h_dist
+ * are host pointers (pinned memory gives the full copy bandwidth; pageable
+ * memory works but the copies are staged by the driver).  Enqueues on `stream`
+ * the copies of the graph into the workspace (cudaMemcpyAsync, 64 MiB pieces),
+ * llp_sssp on them, and the copy of the distances into h_dist; h_dist is
+ * valid once the stream has been synchronised.  The workspace holds the sweep's
+ * scratch followed by the device copy of the graph and of dist:
+ * llp_sssp_host_workspace_size(n, m, offsets_64) bytes.  Same result as
+ * llp_sssp; device status via llp_get_status(ws). */
+size_t llp_sssp_host_workspace_size(int32_t n, int64_t m, int32_t offsets_64);
+llp_status_t llp_sssp_host(const llp_csr_t *h_g, int32_t source, uint32_t *h_dist, const llp_sched_t *sched,
+                           void *ws, size_t ws_bytes, void *stream);
+
 /* Warm start (incremental re-solve).  Algorithm LLP (Sec. 3) reaches the same
  * least solution from any state below it in the lattice order, so a previous
  * result can be the starting state after the graph changed in a way that only

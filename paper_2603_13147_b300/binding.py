@@ -225,6 +225,36 @@ def bfs(g: DeviceGraph, source: int, out=None, sched: Sched | None = None, ws=No
     return _graph_call(lib().llp_bfs, bfs_workspace_size, g, source, out, sched, ws, stream, "llp_bfs")
 
 
+def sssp_host_workspace_size(n: int, m: int, offsets_64: bool = False) -> int:
+    L = lib()
+    L.llp_sssp_host_workspace_size.restype = ctypes.c_size_t
+    return int(L.llp_sssp_host_workspace_size(ctypes.c_int32(n), ctypes.c_int64(m),
+                                              ctypes.c_int32(1 if offsets_64 else 0)))
+
+
+def sssp_host(offsets: torch.Tensor, indices: torch.Tensor, weights: torch.Tensor, source: int,
+              out: torch.Tensor, sched: Sched | None = None, ws=None, stream=None):
+    """llp_sssp_host: the graph and `out` are HOST tensors (pin them for full copy bandwidth);
+    copies, sweep and the copy back are enqueued on `stream`; `out` is valid after it is
+    synchronised.  Returns (out, workspace)."""
+    for t, name in ((offsets, "offsets"), (indices, "indices"), (weights, "weights"), (out, "out")):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous host tensor")
+    if offsets.dtype not in (torch.int32, torch.int64) or indices.dtype != torch.int32 or out.dtype != torch.int32:
+        raise TypeError("offsets int32/int64, indices and out int32")
+    c = Csr()
+    c.n, c.m = offsets.shape[0] - 1, indices.shape[0]
+    c.offsets_64 = 1 if offsets.dtype == torch.int64 else 0
+    c.offsets, c.indices, c.weights = offsets.data_ptr(), indices.data_ptr(), weights.data_ptr()
+    if ws is None:
+        ws = workspace(sssp_host_workspace_size(c.n, c.m, bool(c.offsets_64)))
+    rc = lib().llp_sssp_host(ctypes.byref(c), ctypes.c_int32(source), _ptr(out),
+                             None if sched is None else ctypes.byref(sched), _ptr(ws), ctypes.c_size_t(ws.numel()),
+                             _stream(stream))
+    _check(rc, "llp_sssp_host")
+    return out, ws
+
+
 def _warm_call(fn, wsfn, g: DeviceGraph, source, dist, seeds, sched, ws, stream, what):
     _dev(dist, torch.int32, "dist")
     if seeds is not None and seeds.numel() > 0:

@@ -117,3 +117,26 @@ def test_warm_arguments_rejected_on_host(L):
         assert f(ctypes.byref(c), 10, out, None, 0, None, ws, big, None) == llp.LLP_ERR_INVALID_ARG
         assert f(ctypes.byref(c), 0, out, None, 0, None, ws, ctypes.c_size_t(64), None) == \
             llp.LLP_ERR_WORKSPACE_TOO_SMALL
+
+
+def test_host_entry_arguments_rejected_on_host(L):
+    import paper_2603_13147_b300 as llp
+    c = llp.Csr()
+    c.n, c.m = 10, 5
+    c.offsets = 0x1000
+    ws = ctypes.c_void_p(0x100000)
+    out = ctypes.c_void_p(0x200000)
+    big = ctypes.c_size_t(1 << 30)
+    L.llp_sssp_host_workspace_size.restype = ctypes.c_size_t
+    need = L.llp_sssp_host_workspace_size(ctypes.c_int32(10), ctypes.c_int64(5), ctypes.c_int32(0))
+    L.llp_sssp_workspace_size.restype = ctypes.c_size_t
+    assert need > L.llp_sssp_workspace_size(ctypes.c_int32(10), ctypes.c_int64(5))
+    assert L.llp_sssp_host(ctypes.byref(c), 0, out, None, ws, big, None) == llp.LLP_ERR_INVALID_ARG  # no indices
+    c.m = 0
+    assert L.llp_sssp_host(None, 0, out, None, ws, big, None) == llp.LLP_ERR_INVALID_ARG
+    assert L.llp_sssp_host(ctypes.byref(c), 0, None, None, ws, big, None) == llp.LLP_ERR_INVALID_ARG
+    assert L.llp_sssp_host(ctypes.byref(c), 10, out, None, ws, big, None) == llp.LLP_ERR_INVALID_ARG
+    assert L.llp_sssp_host(ctypes.byref(c), 0, out, None, ctypes.c_void_p(0x100010), big,
+                           None) == llp.LLP_ERR_INVALID_ARG
+    assert L.llp_sssp_host(ctypes.byref(c), 0, out, None, ws, ctypes.c_size_t(128),
+                           None) == llp.LLP_ERR_WORKSPACE_TOO_SMALL

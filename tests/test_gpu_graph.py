@@ -445,3 +445,29 @@ def test_warm_invalid_seed_reported(llp):
     dist = torch.from_numpy(ref.view(np.int32).copy()).cuda()
     _, ws = llp.sssp_warm(dg, 0, dist, torch.tensor([3, g["n"]], dtype=torch.int32, device="cuda"))
     assert llp.get_status(ws)["status"] == llp.LLP_ERR_INVALID_ARG
+
+
+# ------------------------------------------------------ host-buffer entry point
+
+@pytest.mark.parametrize("pinned,off64", [(True, False), (False, False), (True, True)])
+def test_sssp_host_buffers(llp, pinned, off64):
+    for g, s in ((synth.er16k(), 0), (synth.rmat(16, seed=21), None)):
+        s = synth.max_out_degree_vertex(g) if s is None else s
+        off = torch.from_numpy(g["offsets"].astype(np.int64 if off64 else np.int32))
+        idx = torch.from_numpy(g["indices"])
+        w = torch.from_numpy(g["weights"].view(np.int32))
+        out = torch.full((g["n"],), 7, dtype=torch.int32)
+        if pinned:
+            off, idx, w, out = off.pin_memory(), idx.pin_memory(), w.pin_memory(), out.pin_memory()
+        _, ws = llp.sssp_host(off, idx, w, s, out)
+        st = llp.get_status(ws)  # synchronises the stream
+        assert st["status"] == 0
+        assert (out.numpy().view(np.uint32) == oracle.sssp(g["offsets"], g["indices"], g["weights"], s)).all()
+
+
+def test_sssp_host_rejects_device_tensors(llp):
+    g = synth.er16k()
+    off = torch.from_numpy(g["offsets"].astype(np.int32))
+    with pytest.raises(ValueError):
+        llp.sssp_host(off.cuda(), torch.from_numpy(g["indices"]), torch.from_numpy(g["weights"].view(np.int32)), 0,
+                      torch.empty(g["n"], dtype=torch.int32))
