@@ -1124,6 +1124,10 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         if (rc != LLP_OK) return rc;
     }
 
+    // Grid size: small graphs sweep faster on fewer CTAs (their sweeps are short chains of
+    // dependent loads plus a grid barrier whose cost grows with the CTA count); one CTA per
+    // 1,024 vertices, at least 32, at most every co-resident CTA.
+    const int max_blocks = (int)std::max<int64_t>(32, ((int64_t)g->n + 1023) / 1024);
     auto fill = [&](auto &args) {
         args.n = g->n;
         args.source = source;
@@ -1170,7 +1174,7 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         if constexpr (UNIT) {
             if (pull_on) fn = (const void *)graph_sweep_kernel<int64_t, true, true>;
         }
-        return launch_cooperative(fn, threads, 0, 0, kargs, stream);
+        return launch_cooperative(fn, threads, 0, max_blocks, kargs, stream);
     } else {
         GraphArgs<int32_t> args;
         fill(args);
@@ -1181,7 +1185,7 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         if constexpr (UNIT) {
             if (pull_on) fn = (const void *)graph_sweep_kernel<int32_t, true, true>;
         }
-        return launch_cooperative(fn, threads, 0, 0, kargs, stream);
+        return launch_cooperative(fn, threads, 0, max_blocks, kargs, stream);
     }
 }
 
