@@ -33,7 +33,7 @@ WORKLOAD = "rmat22_ef16_sssp"
 # DRAM traffic of the sweep kernel per algorithmic byte, from one ncu capture at
 # R-MAT scale 20 (profiles/graph_sweep_sssp_rmat20_full.md), valid only for the
 # kernel source it was taken from (sha256 prefix of graph_sweep.cu + llp_common.cuh).
-TRAFFIC_CAPTURE = {"src_sha": "6017cc0d6b082c76", "bytes_per_alg_byte": 1.3112}
+TRAFFIC_CAPTURE = {"src_sha": "0742ee827eaec481", "bytes_per_alg_byte": 1.3141}
 
 
 def kernel_src_sha():
