@@ -471,3 +471,18 @@ def test_sssp_host_rejects_device_tensors(llp):
     with pytest.raises(ValueError):
         llp.sssp_host(off.cuda(), torch.from_numpy(g["indices"]), torch.from_numpy(g["weights"].view(np.int32)), 0,
                       torch.empty(g["n"], dtype=torch.int32))
+
+
+def test_stats_report_the_schedule_used(llp):
+    """llp_stats_t echoes the schedule the run used (mode, bucket width, block configuration,
+    local chain) and counts its dense sweeps."""
+    g = synth.er16k()
+    ref = oracle.sssp(g["offsets"], g["indices"], g["weights"], 0)
+    d, st = run_sssp(llp, g, 0, mode=1, delta=64, block_cfg=3, local_chain=16)
+    assert (d == ref).all()
+    assert (st["mode_used"], st["delta_used"], st["block_cfg_used"], st["local_chain_used"]) == (1, 64, 3, 16)
+    assert st["dense_sweeps"] == 0 and st["pull_sweeps"] == 0
+    d, st = run_sssp(llp, g, 0, mode=2)
+    assert (d == ref).all()
+    assert st["mode_used"] == 2 and st["local_chain_used"] == 0 and st["delta_used"] == llp.DELTA_INF
+    assert st["dense_sweeps"] == st["sweeps"] - 2  # all but the first (list) and the last (empty) sweep
