@@ -14,6 +14,8 @@
 namespace llp {
 namespace {
 
+constexpr int kClosureSlices = 8;  // row words per lane per pass (256 words = 8,192 columns)
+
 template <typename OffT>
 struct ClosureArgs {
     int32_t n;
@@ -75,21 +77,39 @@ __global__ void __launch_bounds__(512) closure_kernel(ClosureArgs<OffT> a) {
             if (b == e) continue;
             uint32_t *ru = a.reach + u * (int64_t)a.W;
             uint32_t gained = 0;
-            for (int32_t x0 = 0; x0 < a.W; x0 += 32) {
-                const int32_t x = x0 + lane_id();
-                uint32_t acc = 0;
-                for (OffT y = b; y < e; y++) {
-                    const int32_t wv = __ldg(a.idx + y);
-                    if (k > 1 && !*(volatile const uint8_t *)(prev + wv)) continue;
-                    if (x < a.W) acc |= __ldcg(a.reach + wv * (int64_t)a.W + x);
-                    if (x0 == 0) ors += (lane_id() == 0);
-                }
-                if (x < a.W) {
-                    const uint32_t old = ru[x];
-                    const uint32_t add = acc & ~old;
-                    if (add) {
-                        ru[x] = old | add;
-                        gained += __popc(add);
+            // successors 32 at a time: lane j reads successor j and whether its row changed
+            // in the previous sweep; then the changed rows are ORed into row u, 8 words per
+            // lane (256 words) at a time, all of a successor row's loads in flight together
+            for (OffT y0 = b; y0 < e; y0 += 32) {
+                const OffT y = y0 + lane_id();
+                const int32_t wv = y < e ? __ldg(a.idx + y) : -1;
+                const bool act = wv >= 0 && (k == 1 || *(volatile const uint8_t *)(prev + wv));
+                const uint32_t am = __ballot_sync(0xffffffffu, act);
+                ors += (lane_id() == 0) ? (unsigned long long)__popc(am) : 0ull;
+                for (int32_t c0 = 0; c0 < a.W && am; c0 += 32 * kClosureSlices) {
+                    uint32_t acc[kClosureSlices];
+#pragma unroll
+                    for (int s = 0; s < kClosureSlices; s++) acc[s] = 0u;
+                    for (uint32_t mm = am; mm; mm &= mm - 1u) {
+                        const int32_t w = __shfl_sync(0xffffffffu, wv, __ffs(mm) - 1);
+                        const uint32_t *rw = a.reach + w * (int64_t)a.W;
+#pragma unroll
+                        for (int s = 0; s < kClosureSlices; s++) {
+                            const int32_t x = c0 + 32 * s + lane_id();
+                            if (x < a.W) acc[s] |= __ldcg(rw + x);
+                        }
+                    }
+#pragma unroll
+                    for (int s = 0; s < kClosureSlices; s++) {
+                        const int32_t x = c0 + 32 * s + lane_id();
+                        if (x < a.W) {
+                            const uint32_t old = ru[x];
+                            const uint32_t add = acc[s] & ~old;
+                            if (add) {
+                                ru[x] = old | add;
+                                gained += __popc(add);
+                            }
+                        }
                     }
                 }
             }
