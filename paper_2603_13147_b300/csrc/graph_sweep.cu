@@ -13,10 +13,10 @@
 // (the paper's problem-specific state selection, Sec. 3.2).
 //
 // One cooperative launch runs all sweeps, separated by a bounded grid barrier.
-//   - the worklist of sweep k is a bitmap B_k (one bit per vertex, two buffers
-//     by parity); atomicOr on B_{k+1} deduplicates advances, and the consumer
-//     of sweep k clears B_k as it reads it, so B_k is clean when it becomes
-//     B_{k+2};
+//   - the worklist of sweep k is a bitmap B_k (one bit per vertex, three
+//     buffers used in turn, B_k = bm[k mod 3]); atomicOr on B_{k+1}
+//     deduplicates advances, and a push sweep k clears B_k as it reads it, so
+//     B_k is clean when it becomes B_{k+3};
 //   - a per-vertex class (1: small, out-degree <= small_max; 2: large; 0: no
 //     out-arcs), computed once per call into key[] and a per-32-vertex table, routes
 //     advanced vertices: large ones go to a chunk list (chunks of chunk_edges
