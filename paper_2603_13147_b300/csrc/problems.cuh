@@ -9,6 +9,14 @@ namespace llp {
 
 constexpr unsigned long long kEmptySuitor = 0xFFFFFFFFFFFFFFFFull;
 
+// 64-bit atomic min with acquire-release ordering at device scope (generic
+// address: global or shared memory); returns the previous value.
+__device__ __forceinline__ unsigned long long atomic_min_acq_rel(unsigned long long *p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.acq_rel.gpu.min.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
 // ------------------------------------------------------------ stable marriage
 // Paper Sec. 4.3.  G[m] = next[m], the index into man m's list.  m is
 // forbidden iff the woman w he targets holds a suitor she ranks better; the
@@ -70,15 +78,15 @@ __device__ __forceinline__ unsigned long long propose_chain(int32_t m, int32_t k
                 ww = w[i];
             }
         next[m] = k;
-        __threadfence();
-        const unsigned long long old = atomicMin(best + ww, my);
+        // acq_rel: the release orders next[m] before m becomes w's suitor; the acquire makes
+        // the displaced man's next[] (stored before his own proposal) visible below
+        const unsigned long long old = atomic_min_acq_rel(best + ww, my);
         if (old < my) {  // lost the race: forbidden after all
             k++;
             continue;
         }
         if (old == kEmptySuitor) return proposals;  // w was free: chain ends
         // m displaced old's man, who is forbidden now: carry him
-        __threadfence();
         m = (int32_t)(uint32_t)(old & 0xFFFFFFFFull);
         k = *(volatile int32_t *)(next + m) + 1;
     }
