@@ -31,8 +31,9 @@ SCALE = 22
 WORKLOAD = "rmat22_ef16_sssp"
 
 # DRAM traffic of the sweep kernel per algorithmic byte, from one ncu capture at
-# R-MAT scale 20 (profiles/graph_sweep_sssp_rmat20_full.md), valid only for the
-# kernel source it was taken from (sha256 prefix of graph_sweep.cu + llp_common.cuh).
+# R-MAT scale 20 (dram__bytes_read.sum + dram__bytes_write.sum of one launch), valid
+# only for the kernel source it was taken from (sha256 prefix of graph_sweep.cu +
+# llp_common.cuh).
 TRAFFIC_CAPTURE = {"src_sha": "3d01f74a193b7785", "bytes_per_alg_byte": 1.3116}
 
 

@@ -195,12 +195,27 @@ llp_status_t llp_sssp_warm(const llp_csr_t *g, int32_t source, uint32_t *dist, c
  *  - All calls on a device share the one array: calls that overlap on the GPU
  *    (different streams, or another thread) race and give undefined results.
  *    Serialise them, e.g. on one stream.
- *  - llp_get_status()/llp_sweep_log() cannot be pointed at this scratch; the
- *    device status is not reported (use llp_sssp for diagnostics).
+ *  - The array is a module global: under CUDA's lazy module loading it may be
+ *    reserved only when this module first loads on a device, which can be the
+ *    first llp_sssp_noalloc call; that call then fails with LLP_ERR_CUDA when
+ *    the device has no 64 MiB left.  Every process that loads the library pays
+ *    the 64 MiB on each device where the module is loaded, whether or not it
+ *    calls llp_sssp_noalloc.
+ *  - The return value is the host-side outcome only.  The device-side outcome
+ *    of the last call on the device (LLP_OK, or LLP_ERR_TIMEOUT /
+ *    LLP_ERR_OVERFLOW / LLP_ERR_INVALID_ARG raised during the sweep, in which
+ *    case dist[] is not the distances) is read with llp_sssp_noalloc_status;
+ *    llp_get_status()/llp_sweep_log() cannot be pointed at this scratch.
  *  - Allocates nothing: no cudaMalloc/cudaFree or allocating library call. */
 size_t llp_sssp_noalloc_max_workspace(void);
 llp_status_t llp_sssp_noalloc(const llp_csr_t *g, int32_t source, uint32_t *dist, const llp_sched_t *sched,
                               void *stream);
+/* Device status word of the last llp_sssp_noalloc call on the current device:
+ * copies it into *status after the work queued on `stream` (synchronises the
+ * stream).  Calls from other streams that may still run race with it, as for
+ * llp_sssp_noalloc itself.  Allocates nothing.  LLP_ERR_INVALID_ARG if status
+ * is NULL. */
+llp_status_t llp_sssp_noalloc_status(int32_t *status, void *stream);
 
 /* ------------------------------------------------------------------- BFS
  * Paper Sec. 4.2: G[v] = level; v is forbidden iff an in-neighbour u has

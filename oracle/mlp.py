@@ -10,7 +10,9 @@ Parameter layout (row-major, fp32 on the device, fp64 here):
     W1[F, H1], b1[H1], W2[H1, H2], b2[H2], W3[H2, O], b3[O]
 flattened in that order into one vector.  Heads are contiguous slices of the O
 logits given by ``heads`` (sizes).  Pinned in tests by central finite
-differences of ``loss`` against ``backward``.
+differences of ``loss`` against ``backward``, by a hand-worked forward pass
+with nonzero weights and clipped units, and by three hand-worked Adam steps
+(bias corrections at t = 1, 2, 3).
 """
 from __future__ import annotations
 

@@ -432,6 +432,15 @@ def sssp_noalloc(g: DeviceGraph, source: int, out=None, sched: Sched | None = No
     return out
 
 
+def sssp_noalloc_status(stream=None) -> int:
+    """Device status of the last llp_sssp_noalloc call on the current device
+    (0 = LLP_OK); synchronises the stream."""
+    st = ctypes.c_int32(0)
+    rc = lib().llp_sssp_noalloc_status(ctypes.byref(st), _stream(stream))
+    _check(rc, "llp_sssp_noalloc_status")
+    return int(st.value)
+
+
 # ------------------------------------------------------------------ batched
 
 class Batch(ctypes.Structure):

@@ -1245,6 +1245,19 @@ llp_status_t llp_sssp_noalloc(const llp_csr_t *g, int32_t source, uint32_t *dist
                                    (cudaStream_t)stream);
 }
 
+llp_status_t llp_sssp_noalloc_status(int32_t *status, void *stream) {
+    if (!status) return LLP_ERR_INVALID_ARG;
+    void *scratch = nullptr;
+    const llp_status_t rc = llp::noalloc_scratch(&scratch);
+    if (rc != LLP_OK) return rc;
+    // the status word is the first field of the header at the start of the scratch
+    int32_t st = 0;
+    LLP_CUDA_TRY(cudaMemcpyAsync(&st, scratch, sizeof(st), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    LLP_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    *status = st;
+    return LLP_OK;
+}
+
 size_t llp_sssp_workspace_size(int32_t n, int64_t m) {
     if (n < 1 || m < 0) return 0;
     return llp::carve_graph(nullptr, n, m).bytes;

@@ -224,3 +224,53 @@ def test_adam_first_step_closed_form():
     g = np.array([0.3, -2.0, 1e-3])
     th, m, v = omlp.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.01)
     assert np.allclose(th, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+
+
+def test_mlp_forward_hand_worked():
+    """Forward pass of a 2 -> 2 -> 2 -> 4 network worked out by hand.
+
+    Layer 1 of sample 0: a1 = [1*1 + 2*0.5 + 0.5, 1*(-1) + 2*1 - 3] = [2.5, -2],
+    the ReLU clips the second unit; layer 2: a2 = [2.5*1 - 3, 2.5*2 + 1] = [-0.5, 6],
+    clipped again; logits = [6*0.5 + 1, 6*(-1), 6*0 - 2, 6*1 + 0.5].  A dropped
+    bias, a missing ReLU on either layer or a transposed weight matrix changes them.
+    """
+    F, H1, H2, O = 2, 2, 2, 4
+    W1 = [[1.0, -1.0], [0.5, 1.0]]          # W1[f, h]
+    b1 = [0.5, -3.0]
+    W2 = [[1.0, 2.0], [3.0, -1.0]]          # W2[h1, h2]
+    b2 = [-3.0, 1.0]
+    W3 = [[1.0, 0.0, 2.0, -1.0], [0.5, -1.0, 0.0, 1.0]]
+    b3 = [1.0, 0.0, -2.0, 0.5]
+    th = np.concatenate([np.ravel(a) for a in (W1, b1, W2, b2, W3, b3)])
+    X = np.array([[1.0, 2.0], [0.0, -1.0]])
+    z, _ = omlp.forward(th, X, F, H1, H2, O)
+    # sample 1: a1 = [-0.5 + 0.5, -1 - 3] = [0, -4] -> h1 = 0, h2 = relu(b2) = [0, 1]
+    assert np.array_equal(z, np.array([[4.0, -6.0, -2.0, 6.5], [1.5, -1.0, -2.0, 1.5]]))
+    # two heads of 2 logits; labels (0, 1) and (1, 0): cross-entropy log(1 + e^(other - own))
+    Y = np.array([[0, 1], [1, 0]])
+    want = (np.log1p(np.exp(-10.0)) + np.log1p(np.exp(-8.5)) + np.log1p(np.exp(2.5)) + np.log1p(np.exp(3.5))) / 2
+    assert abs(omlp.loss(th, X, Y, [2, 2], F, H1, H2, O) - want) < 1e-12
+    assert np.array_equal(omlp.predict(th, X, [2, 2], F, H1, H2, O), np.array([[0, 1], [0, 1]]))
+
+
+def test_adam_three_steps_hand_worked():
+    """Three Adam steps (Kingma and Ba, Algorithm 1) on one parameter with gradients
+    1, -2, 0.5, lr 0.1, beta1 0.9, beta2 0.999, worked by hand.  The bias
+    corrections 1 - beta^t at t = 2, 3 are written out (0.19, 0.001999, 0.271,
+    0.002997001), so a correction of the form 1 - beta*t cannot pass."""
+    lr, eps = 0.1, 1e-8
+    th, m, v = omlp.adam_step(np.zeros(1), np.array([1.0]), np.zeros(1), np.zeros(1), 1, lr=lr)
+    assert abs(m[0] - 0.1) < 1e-15 and abs(v[0] - 0.001) < 1e-15
+    th1 = -lr * 1.0 / (1.0 + eps)
+    assert abs(th[0] - th1) < 1e-15
+    th, m, v = omlp.adam_step(th, np.array([-2.0]), m, v, 2, lr=lr)
+    # m2 = 0.9*0.1 + 0.1*(-2) = -0.11; v2 = 0.999*0.001 + 0.001*4 = 0.004999
+    assert abs(m[0] + 0.11) < 1e-15 and abs(v[0] - 0.004999) < 1e-15
+    th2 = th1 - lr * (-0.11 / 0.19) / (np.sqrt(0.004999 / 0.001999) + eps)
+    assert abs(th[0] - th2) < 1e-13
+    th, m, v = omlp.adam_step(th, np.array([0.5]), m, v, 3, lr=lr)
+    # m3 = 0.9*(-0.11) + 0.1*0.5 = -0.049; v3 = 0.999*0.004999 + 0.001*0.25 = 0.005244001
+    assert abs(m[0] + 0.049) < 1e-15 and abs(v[0] - 0.005244001) < 1e-15
+    th3 = th2 - lr * (-0.049 / 0.271) / (np.sqrt(0.005244001 / 0.002997001) + eps)
+    assert abs(th[0] - th3) < 1e-13
+    assert abs(th[0] - (-0.0497206)) < 1e-6

@@ -58,3 +58,50 @@ def test_noalloc_matches_workspace_entry_point_twice(which):
         llp.sssp_noalloc(dg, s, out=out)
         torch.cuda.synchronize()
         assert (llp.as_u32(out) == ref).all()
+
+
+@pytest.mark.gpu
+def test_noalloc_larger_then_smaller_graph_and_no_allocation():
+    """A large graph, then a small one on the same array: the small call's layout
+    sits at other offsets over the large call's leftovers, and must still match the
+    oracle.  Free device memory is unchanged across the second call."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    llp = _llp()
+    gl = synth.rmat(18, seed=7)
+    sl = synth.max_out_degree_vertex(gl)
+    gs = synth.er16k()
+    dl = llp.DeviceGraph.from_host(gl, "cuda")
+    ds = llp.DeviceGraph.from_host(gs, "cuda")
+    outl = torch.empty(gl["n"], dtype=torch.int32, device="cuda")
+    outs = torch.empty(gs["n"], dtype=torch.int32, device="cuda")
+    llp.sssp_noalloc(dl, sl, out=outl)
+    assert llp.sssp_noalloc_status() == 0
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    llp.sssp_noalloc(ds, 0, out=outs)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert llp.sssp_noalloc_status() == 0
+    assert (llp.as_u32(outl) == oracle.sssp(gl["offsets"], gl["indices"], gl["weights"], sl)).all()
+    assert (llp.as_u32(outs) == oracle.sssp(gs["offsets"], gs["indices"], gs["weights"], 0)).all()
+
+
+@pytest.mark.gpu
+def test_noalloc_status_reports_device_timeout():
+    """The device-side outcome is readable: a 1 ns deadline makes the first bounded
+    wait give up (LLP_ERR_TIMEOUT); the next call with the default deadline is clean
+    and correct."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    llp = _llp()
+    g = synth.er16k()
+    dg = llp.DeviceGraph.from_host(g, "cuda")
+    out = torch.empty(g["n"], dtype=torch.int32, device="cuda")
+    llp.sssp_noalloc(dg, 0, out=out, sched=llp.make_sched(deadline_ns=1))
+    assert llp.sssp_noalloc_status() == llp.LLP_ERR_TIMEOUT
+    llp.sssp_noalloc(dg, 0, out=out)
+    assert llp.sssp_noalloc_status() == 0
+    assert (llp.as_u32(out) == oracle.sssp(g["offsets"], g["indices"], g["weights"], 0)).all()
