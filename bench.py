@@ -130,6 +130,41 @@ def make_graph(scale=SCALE):
     return g, s
 
 
+def cpu_info():
+    """Host cores this process may use and the CPU model (for every cpu_baseline)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return cores, model
+
+
+def cpu_time(fn):
+    t = time.perf_counter()
+    r = fn()
+    return time.perf_counter() - t, r
+
+
+def oracle_parallel(tasks, threads):
+    """Runs independent oracle calls (closures) on `threads` host threads (the oracle's C code
+    runs outside the GIL) and returns the wall time."""
+    import concurrent.futures as cf
+    t = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        for f in [ex.submit(fn) for fn in tasks]:
+            f.result()
+    return time.perf_counter() - t
+
+
 def reached_arcs(g, dist_u32):
     deg = np.diff(g["offsets"])
     reached = dist_u32 != 0xFFFFFFFF
@@ -144,6 +179,16 @@ def cpu_oracle_sample(g, s, budget_s=20.0):
     dt = time.perf_counter() - t
     mr, _ = reached_arcs(g, d)
     return mr / dt / 1e9, dt, d
+
+
+def oracle_bfs_levels(g, s):
+    import oracle
+    return oracle.bfs(g["offsets"], g["indices"], s)
+
+
+def oracle_sssp_w(g, w, s):
+    import oracle
+    return oracle.sssp(g["offsets"], g["indices"], w, s)
 
 
 def run_reference(args):
@@ -269,7 +314,8 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     pull_ms = float(np.mean([a.elapsed_time(b) for a, b in pev]))
     pull_st = llp.get_status(ws)
-    pull_same = bool((llp.as_u32(dist_t) == bfs_lv).all())
+    pull_lv = llp.as_u32(dist_t)
+    pull_same = bool((pull_lv == bfs_lv).all())
     del dg_in
 
     # warm start: 0.1 % of the arc weights decreased (w -> max(1, w // 3)); re-solve from the
@@ -301,7 +347,9 @@ def run_gpu(args):
                 (warm_t if warm else cold_t).append(e0.elapsed_time(e1))
     warm_st = llp.get_status(ws)
     warm_same = bool(torch.equal(d_warm, dist_t))
-    del dg2, w2
+    d_warm_host = llp.as_u32(d_warm)
+    w2_host = w2
+    del dg2
 
     # end to end through the C ABI with HOST buffers (llp_sssp_host): every step copies the graph
     # from pinned host memory into a workspace, sweeps, and copies the distances back; steps
@@ -374,18 +422,26 @@ def run_gpu(args):
         "clocks": clocks.summary(),
         "wall_s_timed": t_wall,
     }
+    cpu = rank == 0 and not args.no_cpu_baseline
+    dt22 = None
+    if cpu:
+        gt, dt22, dref = cpu_oracle_sample(g, s)
+        cores, model = cpu_info()
+        line["cpu_baseline"] = {"value": gt, "unit": "GTEPS", "cores": 1, "cpu_model": model,
+                                "host_cores": cores, "kind": "oracle",
+                                "sample": f"full graph, one Dijkstra run ({dt22:.1f} s)"}
+        line["parity_vs_oracle"] = bool((dref == d_host).all())
+        bref = oracle_bfs_levels(g, s)
+        line["bfs"]["parity_vs_oracle"] = bool((bref == bfs_lv).all())
+        line["bfs"]["pull"]["parity_vs_oracle"] = bool((bref == pull_lv).all())
+        line["warm_start"]["parity_vs_oracle"] = bool((oracle_sssp_w(g, w2_host, s) == d_warm_host).all())
     if not args.no_functors:
-        line["functors"] = bench_functors(llp, dev)
+        line["functors"] = bench_functors(llp, dev, cpu=cpu)
     if not args.no_batched:
-        line["batched"] = bench_batched(llp, dev, stream)
+        line["batched"] = bench_batched(llp, dev, stream, cpu=cpu)
         line["batched_graphs"] = bench_batched_graphs(llp, dev)
     if not args.no_learned:
-        line["learned"] = bench_learned(llp, dev, g, s)
-    if rank == 0 and not args.no_cpu_baseline:
-        gt, dt, dref = cpu_oracle_sample(g, s)
-        line["cpu_baseline"] = {"value": gt, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                                "sample": f"full graph, one Dijkstra run ({dt:.1f} s)"}
-        line["parity_vs_oracle"] = bool((dref == d_host).all())
+        line["learned"] = bench_learned(llp, dev, g, s, cpu=cpu, cpu22_s=dt22)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -425,7 +481,55 @@ def smem_peak_gbs(dev):
     return props.multi_processor_count * 128.0 * mhz * 1e6 / 1e9, mhz
 
 
-def bench_batched(llp, dev, stream, div=1):
+def batched_oracle(db, knap, job, sm, every_knap=4):
+    """The oracle on the batched workload on every host core (instances are independent): every
+    job DAG and marriage and every `every_knap`-th knapsack, each checked against the batched
+    engine's output; the knapsack time is scaled to the whole family."""
+    import functools
+    import oracle
+    cores, model = cpu_info()
+    best = db.t["knap_best"].cpu().numpy()
+    comp = db.t["job_completion"].cpu().numpy()
+    wife = db.t["sm_wife"].cpu().numpy()
+    mo = db.sm_man_off_host
+    bad = []
+
+    def k1(i):
+        a, b = knap["item_off"][i], knap["item_off"][i + 1]
+        if oracle.knapsack(knap["w"][a:b], knap["v"][a:b], int(knap["capacity"][i]))[0] != best[i]:
+            bad.append(("knapsack", int(i)))
+
+    def j1(i):
+        j0, j1_ = job["job_off"][i], job["job_off"][i + 1]
+        off = job["succ_offsets"][j0:j1_ + 1] - job["succ_offsets"][j0]
+        ind = job["succ_indices"][job["succ_offsets"][j0]:job["succ_offsets"][j1_]]
+        if not (oracle.job_schedule(job["duration"][j0:j1_], off, ind) == comp[j0:j1_]).all():
+            bad.append(("job", int(i)))
+
+    def s1(i):
+        n = int(sm["n"][i])
+        p0 = sm["pref_off"][i]
+        r = oracle.stable_marriage(sm["men_pref"][p0:p0 + n * n].reshape(n, n),
+                                   sm["women_rank"][p0:p0 + n * n].reshape(n, n))
+        if not (r[0] == wife[mo[i]:mo[i + 1]]).all():
+            bad.append(("marriage", int(i)))
+    kidx = np.arange(0, knap["count"], every_knap)
+    t_k = oracle_parallel([functools.partial(k1, i) for i in kidx], cores)
+    t_j = oracle_parallel([functools.partial(j1, i) for i in range(job["count"])], cores)
+    t_s = oracle_parallel([functools.partial(s1, i) for i in range(sm["count"])], cores)
+    t_k_full = t_k * knap["count"] / len(kidx)
+    total = t_k_full + t_j + t_s
+    count = knap["count"] + job["count"] + sm["count"]
+    return {"value": count / total, "unit": "instances/s", "ms": total * 1e3, "cores": cores, "cpu_model": model,
+            "kind": "oracle",
+            "family_ms": {"knapsack": t_k_full * 1e3, "job": t_j * 1e3, "marriage": t_s * 1e3},
+            "sample": f"every job DAG and marriage, every {every_knap}th knapsack (time scaled by "
+                      f"{knap['count'] / len(kidx):.2f}); instances spread over {cores} host threads",
+            "instances_checked": int(len(kidx) + job["count"] + sm["count"]), "mismatches": bad[:10],
+            "parity_vs_oracle": not bad}
+
+
+def bench_batched(llp, dev, stream, div=1, cpu=True):
     """Batched workload (4,096 knapsack + 2,048 job DAGs + 1,024 stable marriages): one
     persistent launch, autotuned launch shape, replayed from a CUDA graph, against the
     plain engine called once per instance on the same stream (timed on a sample of
@@ -449,6 +553,7 @@ def bench_batched(llp, dev, stream, div=1):
     batched_ms = _ev_time(graph.replay, reps=3)
     bst = llp.get_status(ws)
     total = db.count
+    cpu_base = batched_oracle(db, knap, job, sm) if cpu else None
 
     # knapsack family alone: 3 shared-memory accesses of 4 B per cell (two reads of the previous
     # row, one write), Sigma n_i (W_i + 1) cells
@@ -471,11 +576,20 @@ def bench_batched(llp, dev, stream, div=1):
     best = torch.empty(1, dtype=torch.int32, device=dev)
     kidx = np.arange(0, knap["count"], 16)
 
-    def plain_knap():
-        for i in kidx:
+    def half_times(run, idx):
+        """Times the two interleaved halves of a sample separately; each half's estimate of the
+        whole family, their mean, and their relative spread (the sampling error)."""
+        est = []
+        for part in (idx[0::2], idx[1::2]):
+            est.append(_ev_time(lambda: run(part), reps=1) / max(len(part), 1))
+        return est
+
+    def plain_knap(idx):
+        for i in idx:
             a, b = int(knap["item_off"][i]), int(knap["item_off"][i + 1])
             llp.knapsack(wk[a:b], vk[a:b], int(knap["capacity"][i]), want_row=False, ws=wsk)
-    t_knap = _ev_time(plain_knap, reps=1) * knap["count"] / len(kidx)
+    ek = half_times(plain_knap, kidx)
+    t_knap = float(np.mean(ek)) * knap["count"]
     jidx = np.arange(0, job["count"], 8)
     jgraphs = []
     for i in jidx:
@@ -486,10 +600,12 @@ def bench_batched(llp, dev, stream, div=1):
         jgraphs.append((gj, torch.from_numpy(job["duration"][j0:j1]).to(dev)))
     wsj = llp.workspace(llp.lib().llp_job_schedule_workspace_size(ctypes.c_int32(8192), ctypes.c_int64(0)), dev)
 
-    def plain_job():
-        for gj, dj in jgraphs:
+    def plain_job(idx):
+        for q in idx:
+            gj, dj = jgraphs[q]
             llp.job_schedule(gj, dj, ws=wsj)
-    t_job = _ev_time(plain_job, reps=1) * job["count"] / len(jidx)
+    ej = half_times(plain_job, np.arange(len(jgraphs)))
+    t_job = float(np.mean(ej)) * job["count"]
     sidx = np.arange(0, sm["count"], 8)
     sins = []
     for i in sidx:
@@ -498,18 +614,23 @@ def bench_batched(llp, dev, stream, div=1):
                      torch.from_numpy(sm["women_rank"][p0:p0 + n * n].reshape(n, n)).to(dev)))
     wss = llp.workspace(llp.lib().llp_stable_marriage_workspace_size(ctypes.c_int32(1024)), dev)
 
-    def plain_sm():
-        for a_, b_ in sins:
+    def plain_sm(idx):
+        for q in idx:
+            a_, b_ = sins[q]
             llp.stable_marriage(a_, b_, ws=wss, want_husband=False, want_next=False)
-    t_sm = _ev_time(plain_sm, reps=1) * sm["count"] / len(sidx)
+    es = half_times(plain_sm, np.arange(len(sins)))
+    t_sm = float(np.mean(es)) * sm["count"]
     plain_ms = t_knap + t_job + t_sm
     return {"metric": "instances/s", "instances": total, "batched_ms": batched_ms,
             "batched_inst_per_s": total / (batched_ms * 1e-3), "plain_ms_est": plain_ms,
             "plain_inst_per_s": total / (plain_ms * 1e-3), "speedup": plain_ms / batched_ms,
             "plain_family_ms_est": {"knapsack": t_knap, "job": t_job, "marriage": t_sm},
             "plain_sample": "every 16th knapsack, 8th job DAG and 8th marriage instance, scaled",
+            "plain_sampling_rel_err": {f: abs(e[0] - e[1]) / (e[0] + e[1]) for f, e in
+                                       (("knapsack", ek), ("job", ej), ("marriage", es))},
             "cfg": {"threads": cfg.threads, "knap_unroll": cfg.knap_unroll}, "autotune_ms": tune_ms,
-            "status": bst["status"], "cuda_graph": True, "knapsack_roofline": knap_roof}
+            "status": bst["status"], "cuda_graph": True, "knapsack_roofline": knap_roof,
+            "cpu_baseline": cpu_base}
 
 
 def bench_batched_graphs(llp, dev):
@@ -562,10 +683,16 @@ def bench_batched_graphs(llp, dev):
             "batched_equals_plain_on_16": same, "status": bst["status"], "cuda_graph": True}
 
 
-def bench_functors(llp, dev):
-    """Every other problem of the sweep on its configured workload, device time (CUDA events)."""
+def bench_functors(llp, dev, cpu=True):
+    """Every other problem of the sweep on its configured workload, device time (CUDA events),
+    each beside the oracle on one host core (same instance) and checked against it."""
     import torch
     import synth
+    import oracle
+    cores, model = cpu_info()
+
+    def cpu_entry(sec, sample="the same instance"):
+        return {"ms": sec * 1e3, "cores": 1, "cpu_model": model, "kind": "oracle", "sample": sample}
     out = {}
     # config 1: ER 16,384 / 131,072, source 0 (latency-bound: the input lives in L2)
     g = synth.er16k()
@@ -574,63 +701,97 @@ def bench_functors(llp, dev):
     d = torch.empty(g["n"], dtype=torch.int32, device=dev)
     t = _ev_time(lambda: llp.sssp(dg, 0, out=d, ws=ws), reps=5)
     st = llp.get_status(ws)
+    dres = llp.as_u32(d)
     tb = _ev_time(lambda: llp.bfs(dg, 0, out=d, ws=ws), reps=5)
+    bres = llp.as_u32(d)
     out["er16k_sssp"] = {"ms": t, "sweeps": st["sweeps"], "gteps": g["m"] / (t * 1e-3) / 1e9}
     out["er16k_bfs"] = {"ms": tb, "gteps": g["m"] / (tb * 1e-3) / 1e9}
+    if cpu:
+        tc, ref = cpu_time(lambda: oracle.sssp(g["offsets"], g["indices"], g["weights"], 0))
+        out["er16k_sssp"].update(cpu_baseline=cpu_entry(tc), parity_vs_oracle=bool((dres == ref).all()))
+        tc, ref = cpu_time(lambda: oracle.bfs(g["offsets"], g["indices"], 0))
+        out["er16k_bfs"].update(cpu_baseline=cpu_entry(tc), parity_vs_oracle=bool((bres == ref).all()))
     # config 3: stable marriage, n = 16,384 random and n = 8,192 with one shared men's order
     for name, n, adv, seed in (("marriage16384_random", 16384, False, 3), ("marriage8192_shared", 8192, True, 4)):
         mp, wr = synth.marriage(n, seed=seed, adversarial=adv)
         tmp, twr = torch.from_numpy(mp).to(dev), torch.from_numpy(wr).to(dev)
-        del mp, wr
         wife, _, _, wsm = llp.stable_marriage(tmp, twr)
         t = _ev_time(lambda: llp.stable_marriage(tmp, twr, ws=wsm, want_husband=False, want_next=False), reps=3)
         st = llp.get_status(wsm)
         out[name] = {"ms": t, "proposals": st["aux"], "proposals_per_s": st["aux"] / (t * 1e-3),
-                     "status": st["status"]}
-        del tmp, twr
+                     "matchings_per_s": 1e3 / t, "status": st["status"]}
+        if cpu:
+            tc, ref = cpu_time(lambda: oracle.stable_marriage(mp, wr))
+            out[name].update(cpu_baseline=cpu_entry(tc), parity_vs_oracle=bool((wife.cpu().numpy() == ref[0]).all()),
+                             oracle_proposals=ref[3])
+        del tmp, twr, mp, wr
         torch.cuda.empty_cache()
-    # 0-1 knapsack, one instance n = 2,048, capacity 65,536 (one CTA)
+    # 0-1 knapsack, one instance n = 2,048, capacity 65,536
     w, v = synth.knapsack(2048, 65536, seed=5, stream=77)
     tw, tv = torch.from_numpy(w).to(dev), torch.from_numpy(v).to(dev)
-    _, _, wsk = llp.knapsack(tw, tv, 65536, want_row=False)
+    best, _, wsk = llp.knapsack(tw, tv, 65536, want_row=False)
     t = _ev_time(lambda: llp.knapsack(tw, tv, 65536, want_row=False, ws=wsk), reps=3)
     out["knapsack_2048x65536"] = {"ms": t, "cells_per_s": 2048 * 65537 / (t * 1e-3)}
+    if cpu:
+        tc, ref = cpu_time(lambda: oracle.knapsack(w, v, 65536))
+        out["knapsack_2048x65536"].update(cpu_baseline=cpu_entry(tc), parity_vs_oracle=int(best.item()) == ref[0])
     # job scheduling, one DAG of 1,048,576 jobs (Poisson(3) forward arcs)
     gj, dur = synth.job_dag(1 << 20, seed=5)
     dgj = llp.DeviceGraph.from_host(gj, dev)
     td = torch.from_numpy(dur).to(dev)
-    _, wsj = llp.job_schedule(dgj, td)
+    comp, wsj = llp.job_schedule(dgj, td)
     t = _ev_time(lambda: llp.job_schedule(dgj, td, ws=wsj), reps=3)
     st = llp.get_status(wsj)
     out["job_1M"] = {"ms": t, "jobs": gj["n"], "arcs": gj["m"], "sweeps": st["sweeps"], "status": st["status"]}
+    if cpu:
+        tc, ref = cpu_time(lambda: oracle.job_schedule(dur, gj["offsets"], gj["indices"]))
+        out["job_1M"].update(cpu_baseline=cpu_entry(tc), parity_vs_oracle=bool((comp.cpu().numpy() == ref).all()))
     # transitive closure of a random DAG, n = 8,192, p = 4/n
     gc = synth.random_dag(8192, 4, seed=6)
     dc = llp.DeviceGraph.from_host(gc, dev)
-    _, wsc = llp.transitive_closure(dc)
+    R, wsc = llp.transitive_closure(dc)
     t = _ev_time(lambda: llp.transitive_closure(dc, ws=wsc), reps=3)
     st = llp.get_status(wsc)
     out["closure_dag8192"] = {"ms": t, "sweeps": st["sweeps"], "pairs": st["advances"], "status": st["status"]}
+    if cpu:
+        tc, ref = cpu_time(lambda: oracle.transitive_closure(gc["offsets"], gc["indices"]))
+        out["closure_dag8192"].update(cpu_baseline=cpu_entry(tc),
+                                      parity_vs_oracle=bool((R.cpu().numpy().view(np.uint32) == ref).all()))
     # reduction of 2^28 uint64 (2 GiB, HBM-bound): roofline against the measured copy bandwidth
     x = torch.randint(-(1 << 62), 1 << 62, (1 << 28,), dtype=torch.int64, device=dev)
-    _, wsr = llp.reduce_sum(x)
+    sm, wsr = llp.reduce_sum(x)
     t = _ev_time(lambda: llp.reduce_sum(x, ws=wsr), reps=3)
     peak, kind = peaks()
     gbs = (8 << 28) / (t * 1e-3) / 1e9
     out["reduce_2^28_u64"] = {"ms": t, "GB_per_s": gbs, "frac_of_measured_hbm": gbs / peak}
+    if cpu:
+        xs = x[: 1 << 24].cpu().numpy().view(np.uint64)
+        tc, _ = cpu_time(lambda: oracle.reduce_sum(xs))
+        xh = x.cpu().numpy().view(np.uint64)
+        out["reduce_2^28_u64"].update(
+            cpu_baseline=cpu_entry(tc * 16, sample="the first 2^24 values, time scaled by 16"),
+            parity_vs_oracle=(int(sm.item()) & 0xFFFFFFFFFFFFFFFF) == oracle.reduce_sum(xh))
+        del xh
     del x
     torch.cuda.empty_cache()
     return out
 
 
-def bench_learned(llp, dev, g22, s22):
+def bench_learned(llp, dev, g22, s22, cpu=True, cpu22_s=None):
     """Mixed stream: R-MAT scale 20/22/24 SSSP, 2048x2048 grid SSSP, closure of a random
-    DAG (n=8192, p=4/n).  Learned schedule (network on the device) against the fixed
-    heuristic schedule of the plain engine; end-to-end device time of the stream."""
+    DAG (n=8192, p=4/n).  Three arms on the same device, end-to-end device time of the stream:
+    the learned schedule (network on the device), the plain engine's fixed heuristic schedule,
+    and the plain engine autotuned per item (coordinate search over mode, bucket width, block
+    configuration and local chain, each candidate timed; the search itself is not counted).
+    Every item's result is compared with the heuristic run (bit-exact) and, on the host, with
+    the oracle (one core; R-MAT 22 reuses the headline's oracle run)."""
     import torch
     import synth
+    import oracle
     from paper_2603_13147_b300 import sched as S
     if not os.path.exists(S.MODEL_PATH):
         return {"unavailable": "no trained scheduler model in the package"}
+    cores, model = cpu_info()
     params = S.load_model(device=dev)
     items = []
     for scale in (20, 22, 24):
@@ -639,7 +800,8 @@ def bench_learned(llp, dev, g22, s22):
         items.append((f"rmat{scale}_sssp", gg, src))
     items.append(("grid2048_sssp", synth.grid_graph(2048, 2048, 1, 1000, seed=6), 0))
     res = {}
-    tot_h = tot_l = 0.0
+    tot_h = tot_l = tot_a = tot_cpu = 0.0
+    parity_all = True
     for name, gg, src in items:
         dg = llp.DeviceGraph.from_host(gg, dev)
         ws = llp.workspace(llp.sssp_workspace_size(gg["n"], gg["m"]), dev)
@@ -649,20 +811,72 @@ def bench_learned(llp, dev, g22, s22):
         ls = S.learned_sched(params)
         tl = _ev_time(lambda: llp.sssp(dg, src, out=out, ws=ws, sched=ls), reps=3)
         st = llp.get_status(ws)
-        res[name] = {"heuristic_ms": th, "learned_ms": tl, "learned_schedule": [st["mode_used"], st["delta_used"],
-                     st["block_cfg_used"]], "bit_exact": bool(torch.equal(ref, out))}
+        same_l = bool(torch.equal(ref, out))
+        wmax = S.sampled_wmax(gg)
+        t_search = time.perf_counter()
+        label, log, _ = S.label_graph(dg, src, False, wmax, ws=ws)
+        t_search = time.perf_counter() - t_search
+        asch = S.label_to_sched(label, wmax)
+        ta = _ev_time(lambda: llp.sssp(dg, src, out=out, ws=ws, sched=asch), reps=3)
+        gw_best = 0
+        for gw in (1, 2, 4, 8):  # the dense-sweep group width, a fifth coordinate
+            asch.group_words = gw
+            tg = _ev_time(lambda: llp.sssp(dg, src, out=out, ws=ws, sched=asch), reps=3)
+            if tg < ta * 0.97:
+                ta, gw_best = tg, gw
+        asch.group_words = gw_best
+        ta = _ev_time(lambda: llp.sssp(dg, src, out=out, ws=ws, sched=asch), reps=3)
+        same_a = bool(torch.equal(ref, out))
+        ent = {"heuristic_ms": th, "learned_ms": tl, "autotuned_ms": ta,
+               "learned_schedule": [st["mode_used"], st["delta_used"], st["block_cfg_used"],
+                                    st["local_chain_used"]],
+               "autotuned_schedule": {"mode": int(label[0]), "delta": S.delta_of_class(int(label[1]), wmax),
+                                      "block_cfg": int(label[2]) + 1,
+                                      "local_chain": S.CHAIN_OF_CLASS[int(label[3])],
+                                      "group_words": gw_best},
+               "autotune_candidates": len(log), "autotune_search_s": t_search,
+               "bit_exact": same_l and same_a}
+        if cpu:
+            if name == "rmat22_sssp" and cpu22_s is not None:
+                tc = cpu22_s
+                ok = None
+            else:
+                tc, dref = cpu_time(lambda: oracle.sssp(gg["offsets"], gg["indices"], gg["weights"], src))
+                ok = bool((llp.as_u32(ref) == dref).all())
+                parity_all &= ok
+            ent["cpu_baseline_ms"] = tc * 1e3
+            ent["parity_vs_oracle"] = ok
+            tot_cpu += tc
+        res[name] = ent
         tot_h += th
         tot_l += tl
+        tot_a += ta
         del dg, ws, out
         torch.cuda.empty_cache()
     gc = synth.random_dag(8192, 4, seed=6)
     dc = llp.DeviceGraph.from_host(gc, dev)
     R, wsc = llp.transitive_closure(dc)
-    tc = _ev_time(lambda: llp.transitive_closure(dc, ws=wsc), reps=3)
-    res["closure8192"] = {"heuristic_ms": tc, "learned_ms": tc, "note": "no schedule choice"}
-    tot_h += tc
-    tot_l += tc
-    return {"stream_heuristic_ms": tot_h, "stream_learned_ms": tot_l, "speedup": tot_h / tot_l, "items": res}
+    tc_ms = _ev_time(lambda: llp.transitive_closure(dc, ws=wsc), reps=3)
+    res["closure8192"] = {"heuristic_ms": tc_ms, "learned_ms": tc_ms, "autotuned_ms": tc_ms,
+                          "note": "no schedule choice"}
+    if cpu:
+        tcc, Rref = cpu_time(lambda: oracle.transitive_closure(gc["offsets"], gc["indices"]))
+        ok = bool((R.cpu().numpy().view(np.uint32) == Rref).all())
+        parity_all &= ok
+        res["closure8192"].update(cpu_baseline_ms=tcc * 1e3, parity_vs_oracle=ok)
+        tot_cpu += tcc
+    tot_h += tc_ms
+    tot_l += tc_ms
+    tot_a += tc_ms
+    line = {"stream_heuristic_ms": tot_h, "stream_learned_ms": tot_l, "stream_autotuned_ms": tot_a,
+            "speedup_vs_heuristic": tot_h / tot_l, "speedup_vs_autotuned": tot_a / tot_l,
+            "items": res}
+    if cpu:
+        line["cpu_baseline"] = {"ms": tot_cpu * 1e3, "cores": 1, "cpu_model": model, "kind": "oracle",
+                                "sample": "every item of the stream on one host core (Dijkstra per SSSP item, "
+                                          "Warshall for the closure)"}
+        line["parity_vs_oracle"] = parity_all
+    return line
 
 
 def main():

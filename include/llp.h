@@ -93,6 +93,14 @@ typedef struct llp_sched {
     int32_t pull_permille;  /* llp_bfs_pull: a sweep runs pull-style over the in-arcs when its frontier
                                holds more than about m * pull_permille / 1000 out-arcs (0 = 200);
                                < 0 = never pull */
+    int32_t group_words;    /* graph sweep: bitmap words (32 vertices each) per work item of a dense
+                               sweep, 1, 2, 4 or 8; 0 = auto (the widest that still gives every warp
+                               of the grid about three items) */
+    int32_t fixed_memo;     /* SSSP with finite delta: 1 = fixed-state memoization (paper Sec. 3,
+                               "memoization through fixed states"): once a bucket empties, every
+                               vertex below its bound is final; a relaxation that meets such a
+                               vertex marks it in a bitmap, and later relaxations test the bit
+                               instead of reading d(v).  0 = off */
 } llp_sched_t;
 
 /* Work-block configurations of the graph sweep: (small-vertex degree limit,

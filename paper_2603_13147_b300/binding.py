@@ -43,7 +43,8 @@ class Sched(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("delta", ctypes.c_uint32), ("block_cfg", ctypes.c_int32),
                 ("dense_permille", ctypes.c_int32), ("use_mlp", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("deadline_ns", ctypes.c_int64), ("mlp_params", ctypes.c_void_p), ("local_chain", ctypes.c_int32),
-                ("pull_permille", ctypes.c_int32)]
+                ("pull_permille", ctypes.c_int32), ("group_words", ctypes.c_int32),
+                ("fixed_memo", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -88,8 +89,10 @@ def status_string(code: int) -> str:
 
 
 def make_sched(mode=0, delta=0, block_cfg=0, dense_permille=0, use_mlp=0, threads=0, deadline_ns=0,
-               mlp_params=None, local_chain=0, pull_permille=0) -> Sched:
+               mlp_params=None, local_chain=0, pull_permille=0, group_words=0, fixed_memo=0) -> Sched:
     s = Sched()
+    s.group_words = group_words
+    s.fixed_memo = fixed_memo
     s.local_chain = local_chain
     s.pull_permille = pull_permille
     s.mode, s.delta, s.block_cfg, s.dense_permille = mode, delta, block_cfg, dense_permille

@@ -2,9 +2,7 @@
 // SSSP (paper Sec. 4.1) and BFS (paper Sec. 4.2).
 //
 // State G[v] = d(v) (uint32, 0xFFFFFFFF = "infinity"), kept during the run in
-// the high half of a 64-bit word key[v] = d(v) << 32 | class(v) so that the one
-// load that evaluates the predicate also yields how v is scheduled; the result
-// is copied to dist[] when the run ends.  A vertex v is forbidden
+// the caller's dist[] itself (no copy at the end).  A vertex v is forbidden
 // when some arc (u, v) offers d(u) + w(u, v) < d(v); the advance lowers d(v)
 // with an atomic min, the lock-free monotone update whose requirements the
 // paper lists in Sec. 3.2 (atomic, monotone, progress detection).  The
@@ -18,17 +16,19 @@
 //     deduplicates advances, and a push sweep k clears B_k as it reads it, so
 //     B_k is clean when it becomes B_{k+3};
 //   - a per-vertex class (1: small, out-degree <= small_max; 2: large; 0: no
-//     out-arcs), computed once per call into key[] and a per-32-vertex table, routes
+//     out-arcs), computed once per call into a per-32-vertex table, routes
 //     advanced vertices: large ones go to a chunk list (chunks of chunk_edges
 //     arcs, one per warp, so hubs spread over the grid), small ones either to a
 //     list (sparse sweep, warp-aggregated appends) or only to the bitmap (dense
 //     sweep: fire-and-forget atomicOr, the next sweep scans the bitmap like the
 //     paper's all-indices solver, without any shared counter in the hot loop);
-//   - small vertices are expanded 32 per warp, arcs balanced across the lanes;
-//   - the advance itself is a fire-and-forget 64-bit atomic min on key[v]
-//     issued when the candidate beats the value just read (a stale read only
-//     costs a redundant visit: distances only decrease; the class bits are the
-//     same on both sides of the min);
+//   - small vertices are expanded 32 per warp, arcs balanced across the lanes,
+//     kUnroll arcs per lane in flight (the random reads of d(v) are the
+//     bottleneck; they need many independent loads per lane to reach the
+//     device's random-access rate);
+//   - the advance itself is a fire-and-forget atomic min on dist[v] issued
+//     when the candidate beats the value just read (a stale read only costs a
+//     redundant visit: distances only decrease);
 //   - with a finite bucket width delta (the paper's bucket worklist, Sec. 3.3)
 //     only advances with d below the current bucket bound enter the next
 //     worklist; the others wait in a far list filtered when the near worklist
@@ -50,6 +50,10 @@ namespace llp {
 
 llp_status_t enqueue_learned_schedule(const llp_csr_t *g, int32_t source, bool unit, const float *params,
                                       WsHeader *h, cudaStream_t st);
+size_t lb_workspace_bytes(int32_t n, int64_t m);
+llp_status_t lb_launch(bool unit, const llp_csr_t *g, int32_t source, uint32_t *dist, uint32_t *bm0, uint32_t *bm1,
+                       void *lists, WsHeader *h, long long deadline_ns, int32_t mode, unsigned long long dense_arcs,
+                       const int32_t *seeds, int32_t n_seeds, cudaStream_t stream);
 
 namespace {
 
@@ -64,7 +68,14 @@ __host__ __device__ inline BlockCfg block_cfg_of(int c) {
     return c == 1 ? BlockCfg{32, 256} : (c == 3 ? BlockCfg{128, 512} : BlockCfg{64, 256});
 }
 
-constexpr int kUnroll = 4;  // arcs per lane in flight
+#ifndef LLP_SWEEP_UNROLL
+#define LLP_SWEEP_UNROLL 4
+#endif
+#ifndef LLP_SWEEP_MIN_BLOCKS
+#define LLP_SWEEP_MIN_BLOCKS 2
+#endif
+constexpr int kUnroll = LLP_SWEEP_UNROLL;  // arcs per lane in flight (push sweeps)
+constexpr int kPullUnroll = 4;  // in-arcs per lane and round (pull sweeps)
 #ifndef LLP_DENSE_GROUP_WORDS
 #define LLP_DENSE_GROUP_WORDS 8
 #endif
@@ -78,8 +89,7 @@ struct GraphArgs {
     const OffT *off;
     const int32_t *idx;
     const uint32_t *w;
-    uint32_t *dist;                 // output
-    unsigned long long *key;        // d << 32 | class during the run
+    uint32_t *dist;                 // state during the run, and the output
     uint2 *cls;      // per 32 vertices: x = has out-arcs, y = large
     uint32_t *bm[3]; // frontier bitmaps, B_k = bm[k % 3]
     // pull sweeps (BFS only): in-arcs, visited bitmap, frontier size that selects them
@@ -91,6 +101,8 @@ struct GraphArgs {
     int2 *chunk[2];
     int2 *far[2];
     uint32_t far_cap;
+    uint32_t *trace;  // LLP_SWEEP_TRACE builds only: per sweep and CTA, first-warp and CTA finish times
+    uint32_t *fixed;  // fixed-state memoization (NULL: off): bit v set = d(v) is final
     WsHeader *h;
     uint32_t delta;  // kInf: no buckets
     int32_t mode;
@@ -100,6 +112,7 @@ struct GraphArgs {
     int32_t cfg;
     int32_t use_dev_sched;  // 1: take mode/delta/cfg from the header (learned scheduler)
     int32_t local_chain;    // batches per worklist item of the local chain, 0 = off
+    int32_t group_words;    // dense sweeps: bitmap words per item (1, 2, 4, 8), 0 = from the grid size
     long long deadline_ns;
     // warm start: G starts from dist[] (upper bounds of the distances) and the first
     // worklist is seeds[0..n_seeds) instead of the source alone
@@ -111,9 +124,11 @@ struct GraphArgs {
 struct SweepCtx {
     // schedule of this run (from the arguments, or chosen on the device)
     int32_t mode, cfg, small_max, chunk_edges;
+    int32_t gw;                    // dense sweeps: bitmap words per item
     uint32_t delta;
     uint32_t k;                    // current sweep
     unsigned long long bucket_hi;  // exclusive bound of the current bucket
+    unsigned long long fixed_lo;   // every d below it is final (the previous bucket's bound)
     uint32_t fa;                   // far-list generation
     bool dense_next;               // small advances only set their bitmap bit
     bool pull = false;             // this sweep runs over the in-arcs
@@ -158,11 +173,17 @@ __device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
 __device__ __forceinline__ void red_and(uint32_t *p, uint32_t v) {
     asm volatile("red.relaxed.gpu.global.and.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ void red_min64(unsigned long long *p, unsigned long long v) {
-    asm volatile("red.relaxed.gpu.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void red_min32(uint32_t *p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.min.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ uint32_t key_dist(unsigned long long kv) { return (uint32_t)(kv >> 32); }
+// Class of v (0: no out-arcs, 1: small, 2: large) from the per-32-vertex table.
+template <typename OffT>
+__device__ __forceinline__ uint32_t class_of(const GraphArgs<OffT> &a, int32_t v) {
+    const uint2 cw = __ldg(&a.cls[(uint32_t)v >> 5]);
+    const uint32_t bit = 1u << (v & 31);
+    return (cw.x & bit) ? ((cw.y & bit) ? 2u : 1u) : 0u;
+}
 
 // Append the vertices v[j] that entered the frontier bitmap of sweep k+1 for
 // the first time (newly[j]) to the small-vertex list or, as chunks, to the
@@ -282,31 +303,43 @@ __device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, const bool (
 }
 
 // Evaluate forbidden(v) against candidate distances and advance, for up to
-// kUnroll arcs per lane.  Warp-collective.
+// kUnroll arcs per lane.  cand = d(u) + w(u, v) in 32 bits; ovf marks a sum that
+// does not fit (a finite length >= 0xFFFFFFFF).  Warp-collective.
 template <typename OffT>
 __device__ __forceinline__ void relax_multi(const GraphArgs<OffT> &a, const bool (&ok)[kUnroll],
-                                            const int32_t (&v)[kUnroll], const uint64_t (&cand64)[kUnroll],
-                                            SweepCtx &c) {
-    unsigned long long kv[kUnroll];
+                                            const int32_t (&v)[kUnroll], const uint32_t (&cand)[kUnroll],
+                                            const bool (&ovf)[kUnroll], SweepCtx &c) {
+    uint32_t dv[kUnroll];
+    bool live[kUnroll];
 #pragma unroll
-    for (int j = 0; j < kUnroll; j++) kv[j] = ok[j] ? __ldcg(a.key + v[j]) : 0ull;
+    for (int j = 0; j < kUnroll; j++) live[j] = ok[j];
+    if (a.fixed) {
+        // fixed-state memoization: a target known to be final is not read
+        uint32_t fw[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) fw[j] = ok[j] ? __ldcg(a.fixed + (v[j] >> 5)) : 0u;
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) live[j] = ok[j] && ((fw[j] >> (v[j] & 31)) & 1u) == 0;
+    }
+#pragma unroll
+    for (int j = 0; j < kUnroll; j++) dv[j] = live[j] ? __ldcg(a.dist + v[j]) : 0u;
     bool near[kUnroll], far[kUnroll];
-    uint32_t cls[kUnroll];
-    bool any_far = false;
+    bool any_far = false, any_near = false;
 #pragma unroll
     for (int j = 0; j < kUnroll; j++) {
         bool improved = false;
-        cls[j] = (uint32_t)kv[j] & 3u;
-        if (ok[j]) {
-            if (cand64[j] >= (uint64_t)kInf) {
+        if (live[j]) {
+            if (ovf[j]) {
                 set_status(a.h, LLP_ERR_OVERFLOW);
-            } else if ((uint32_t)cand64[j] < key_dist(kv[j])) {
-                red_min64(a.key + v[j], (cand64[j] << 32) | cls[j]);
+            } else if (cand[j] < dv[j]) {
+                red_min32(a.dist + v[j], cand[j]);
                 improved = true;
+            } else if (a.fixed && (unsigned long long)dv[j] < c.fixed_lo) {
+                red_or(a.fixed + (v[j] >> 5), 1u << (v[j] & 31));  // below every pending bucket: final
             }
         }
         c.adv += improved;
-        near[j] = improved && cand64[j] < c.bucket_hi;
+        near[j] = improved && (unsigned long long)cand[j] < c.bucket_hi;
         far[j] = improved && !near[j];
         any_far |= far[j];
     }
@@ -315,14 +348,14 @@ __device__ __forceinline__ void relax_multi(const GraphArgs<OffT> &a, const bool
 #pragma unroll
         for (int j = 0; j < kUnroll; j++) {
             cnt += far[j];
-            if (far[j]) fmin = min(fmin, (uint32_t)cand64[j]);
+            if (far[j]) fmin = min(fmin, cand[j]);
         }
         uint32_t slot = warp_reserve(cnt, &a.h->n_far[c.fa % 3]);
 #pragma unroll
         for (int j = 0; j < kUnroll; j++) {
             if (!far[j]) continue;
             if (slot < a.far_cap) {
-                a.far[c.fa & 1][slot] = make_int2(v[j], (int)(uint32_t)cand64[j]);
+                a.far[c.fa & 1][slot] = make_int2(v[j], (int)cand[j]);
             } else {
                 near[j] = true;  // far list full: keep it in the near worklist (still correct)
             }
@@ -330,10 +363,14 @@ __device__ __forceinline__ void relax_multi(const GraphArgs<OffT> &a, const bool
         }
         if (cnt) atomicMin(&a.h->far_min[c.fa % 3], fmin);
     }
-    bool any_near = false;
 #pragma unroll
     for (int j = 0; j < kUnroll; j++) any_near |= near[j];
-    if (__any_sync(0xffffffffu, any_near)) push_near(a, near, v, cls, c);
+    if (__any_sync(0xffffffffu, any_near)) {
+        uint32_t cls[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) cls[j] = near[j] ? class_of(a, v[j]) : 0u;
+        push_near(a, near, v, cls, c);
+    }
 }
 
 // Expand the out-arcs of up to 32 small vertices (one per lane) edge-balanced
@@ -347,7 +384,7 @@ __device__ __forceinline__ void expand_group(const GraphArgs<OffT> &a, bool vali
     OffT beg = 0;
     if (valid) {
         const uint32_t sk = skip ? __ldcg(skip + (u >> 5)) : 0u;
-        du = key_dist(__ldcg(a.key + u));
+        du = __ldcg(a.dist + u);
         beg = __ldg(a.off + u);
         const OffT end = __ldg(a.off + u + 1);
         valid = ((sk >> (u & 31)) & 1u) == 0;
@@ -364,9 +401,9 @@ __device__ __forceinline__ void expand_group(const GraphArgs<OffT> &a, bool vali
     const uint32_t excl = incl - deg;
     c.edges += (lane_id() == 0) ? total : 0;
     for (uint32_t base = 0; base < total; base += 32 * kUnroll) {
-        bool ok[kUnroll];
+        bool ok[kUnroll], ovf[kUnroll];
         int32_t v[kUnroll];
-        uint64_t cand[kUnroll];
+        uint32_t cand[kUnroll];
 #pragma unroll
         for (int j = 0; j < kUnroll; j++) {
             const uint32_t t = base + 32 * j + lane_id();
@@ -385,12 +422,13 @@ __device__ __forceinline__ void expand_group(const GraphArgs<OffT> &a, bool vali
             uint32_t w = 0;
             if (ok[j]) {
                 const OffT e = bo + (OffT)(t - ex);
-                v[j] = __ldg(a.idx + e);
-                w = UNIT ? 1u : __ldg(a.w + e);
+                v[j] = __ldcs(a.idx + e);
+                w = UNIT ? 1u : __ldcs(a.w + e);
             }
-            cand[j] = (uint64_t)dq + w;
+            cand[j] = dq + w;
+            ovf[j] = cand[j] < dq || cand[j] == kInf;
         }
-        relax_multi(a, ok, v, cand, c);
+        relax_multi(a, ok, v, cand, ovf, c);
     }
 }
 
@@ -426,7 +464,40 @@ __device__ __forceinline__ void drain_local(const GraphArgs<OffT> &a, SweepCtx &
     }
 }
 
-// One chunk (<= chunk_edges arcs) of one large vertex.
+// One chunk (<= chunk_edges arcs) of one large vertex u: chunk y of the row
+// [b0, e0), relaxed from d(u) = du.  Warp-collective; the arguments are
+// warp-uniform.
+template <typename OffT, bool UNIT>
+__device__ __forceinline__ void chunk_body(const GraphArgs<OffT> &a, int32_t y, uint32_t du, OffT b0, OffT e0,
+                                           SweepCtx &c) {
+    const OffT beg = b0 + (OffT)y * (OffT)c.chunk_edges;
+    const OffT end = min(e0, beg + (OffT)c.chunk_edges);
+    c.items += (lane_id() == 0 && y == 0);
+    c.edges += (lane_id() == 0) ? (unsigned long long)(end - beg) : 0ull;
+    for (OffT base = beg; base < end; base += 32 * kUnroll) {
+        bool ok[kUnroll], ovf[kUnroll];
+        int32_t v[kUnroll];
+        uint32_t cand[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) {
+            const OffT e = base + 32 * j + lane_id();
+            ok[j] = e < end;
+            v[j] = 0;
+            uint32_t w = 0;
+            if (ok[j]) {
+                v[j] = __ldcs(a.idx + e);
+                w = UNIT ? 1u : __ldcs(a.w + e);
+            }
+            cand[j] = du + w;
+            ovf[j] = cand[j] < du || cand[j] == kInf;
+        }
+        relax_multi(a, ok, v, cand, ovf, c);
+    }
+}
+
+// One chunk item (vertex u, chunk y): skipped when u was advanced again during
+// this sweep (sweep k+1 expands it with the newer distance); the first chunk of
+// a vertex clears its bit in B_k.  Warp-collective.
 template <typename OffT, bool UNIT>
 __device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item, SweepCtx &c) {
     const int32_t u = item.x;
@@ -435,50 +506,30 @@ __device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item
     OffT b0 = 0, e0 = 0;
     if (lane_id() == 0) {
         nxt = __ldcg(c.bm_next + (u >> 5));
-        du = key_dist(__ldcg(a.key + u));
+        du = __ldcg(a.dist + u);
         b0 = __ldg(a.off + u);
         e0 = __ldg(a.off + u + 1);
         if (item.y == 0) red_and(c.bm_cur + (u >> 5), ~bit);
     }
     nxt = __shfl_sync(0xffffffffu, nxt, 0);
-    if (nxt & bit) return;  // advanced again meanwhile: sweep k+1 handles it (warp-uniform)
+    if (nxt & bit) return;  // warp-uniform
     du = __shfl_sync(0xffffffffu, du, 0);
     b0 = __shfl_sync(0xffffffffu, b0, 0);
     e0 = __shfl_sync(0xffffffffu, e0, 0);
-    const OffT beg = b0 + (OffT)item.y * (OffT)c.chunk_edges;
-    const OffT end = min(e0, beg + (OffT)c.chunk_edges);
-    c.items += (lane_id() == 0 && item.y == 0);
-    c.edges += (lane_id() == 0) ? (unsigned long long)(end - beg) : 0ull;
-    for (OffT base = beg; base < end; base += 32 * kUnroll) {
-        bool ok[kUnroll];
-        int32_t v[kUnroll];
-        uint64_t cand[kUnroll];
-#pragma unroll
-        for (int j = 0; j < kUnroll; j++) {
-            const OffT e = base + 32 * j + lane_id();
-            ok[j] = e < end;
-            v[j] = 0;
-            uint32_t w = 0;
-            if (ok[j]) {
-                v[j] = __ldg(a.idx + e);
-                w = UNIT ? 1u : __ldg(a.w + e);
-            }
-            cand[j] = (uint64_t)du + w;
-        }
-        relax_multi(a, ok, v, cand, c);
-    }
+    chunk_body<OffT, UNIT>(a, item.y, du, b0, e0, c);
+    if (c.chain_on) drain_local<OffT, UNIT>(a, c);
 }
 
-// Dense sweep item: kGroupWords bitmap words (32 vertices each), loaded with
+// Dense sweep item: c.gw (<= kGroupWords) bitmap words (32 vertices each), loaded with
 // one coalesced access.  The small vertices whose bit is set (and not set again
 // for the next sweep) are compacted across the words, 32 per expansion, so a
 // warp's lanes stay filled when few vertices of a word are active.  The words
 // are cleared.
 template <typename OffT, bool UNIT>
 __device__ __forceinline__ void scan_words(const GraphArgs<OffT> &a, int64_t g, SweepCtx &c) {
-    const int64_t wi = g * kGroupWords + lane_id();
+    const int64_t wi = g * c.gw + lane_id();
     uint32_t act = 0;
-    if (lane_id() < kGroupWords && wi < a.nwords) {
+    if (lane_id() < c.gw && wi < a.nwords) {
         const uint32_t b = __ldcg(c.bm_cur + wi);
         const uint32_t large = __ldg(&a.cls[wi].y);
         const uint32_t again = __ldcg(c.bm_next + wi);
@@ -509,19 +560,19 @@ __device__ __forceinline__ void scan_words(const GraphArgs<OffT> &a, int64_t g, 
         const uint32_t ex = __shfl_sync(0xffffffffu, excl, owner);
         const uint32_t word = __shfl_sync(0xffffffffu, act, owner);
         int32_t u = 0;
-        if (ok) u = (int32_t)((g * kGroupWords + owner) * 32 + __fns(word, 0, (int)(t - ex) + 1));
+        if (ok) u = (int32_t)((g * c.gw + owner) * 32 + __fns(word, 0, (int)(t - ex) + 1));
         expand_group<OffT, UNIT>(a, ok, u, c);
     }
 }
 
 // ---- pull sweeps (BFS over in-arcs; levels are exact per sweep, so the first
 // in-neighbour found in the frontier B_k gives the least level k)
-constexpr int kPullLaneRounds = 2;  // per-lane rounds of kUnroll in-arcs before the warp helps
+constexpr int kPullLaneRounds = 2;  // per-lane rounds of kPullUnroll in-arcs before the warp helps
 
 // Up to 32 unreached vertices, one per lane (ok), v in bitmap word slot `owner`
-// of the item.  Each lane scans its in-arcs kUnroll at a time and stops at
+// of the item.  Each lane scans its in-arcs kPullUnroll at a time and stops at
 // the first source u with u in B_k; a vertex still open after
-// kPullLaneRounds rounds is finished by the whole warp, 32 * kUnroll in-arcs
+// kPullLaneRounds rounds is finished by the whole warp, 32 * kPullUnroll in-arcs
 // per step.  A vertex found gets level d(u) + 1 and enters B_{k+1} (if it has
 // out-arcs) and the worklists of sweep k+1.  Warp-collective.
 template <typename OffT>
@@ -540,18 +591,18 @@ __device__ __forceinline__ void pull_batch(const GraphArgs<OffT> &a, bool ok, in
     for (int r = 0; r < kPullLaneRounds; r++) {
         const bool act = ok && !found && b < e;
         if (!__any_sync(0xffffffffu, act)) break;
-        int32_t u[kUnroll];
-        bool in[kUnroll];
+        int32_t u[kPullUnroll];
+        bool in[kPullUnroll];
 #pragma unroll
-        for (int j = 0; j < kUnroll; j++) {
+        for (int j = 0; j < kPullUnroll; j++) {
             in[j] = act && b + (OffT)j < e;
             u[j] = in[j] ? __ldg(a.in_idx + b + j) : 0;
         }
-        uint32_t fw[kUnroll];
+        uint32_t fw[kPullUnroll];
 #pragma unroll
-        for (int j = 0; j < kUnroll; j++) fw[j] = in[j] ? __ldcg(c.bm_cur + (u[j] >> 5)) : 0u;
+        for (int j = 0; j < kPullUnroll; j++) fw[j] = in[j] ? __ldcg(c.bm_cur + (u[j] >> 5)) : 0u;
 #pragma unroll
-        for (int j = 0; j < kUnroll; j++) {
+        for (int j = 0; j < kPullUnroll; j++) {
             if (in[j] && !found) {
                 exam++;
                 if ((fw[j] >> (u[j] & 31)) & 1u) {
@@ -560,7 +611,7 @@ __device__ __forceinline__ void pull_batch(const GraphArgs<OffT> &a, bool ok, in
                 }
             }
         }
-        if (act) b = (e - b > (OffT)kUnroll) ? b + (OffT)kUnroll : e;
+        if (act) b = (e - b > (OffT)kPullUnroll) ? b + (OffT)kPullUnroll : e;
     }
     uint32_t rest = __ballot_sync(0xffffffffu, ok && !found && b < e);
     while (rest) {
@@ -570,24 +621,24 @@ __device__ __forceinline__ void pull_batch(const GraphArgs<OffT> &a, bool ok, in
         const OffT el = __shfl_sync(0xffffffffu, e, l);
         int32_t hit = -1;
         uint32_t seen = 0;
-        for (OffT base = bl; base < el && hit < 0; base += 32 * kUnroll) {
-            int32_t u[kUnroll];
-            bool in[kUnroll];
+        for (OffT base = bl; base < el && hit < 0; base += 32 * kPullUnroll) {
+            int32_t u[kPullUnroll];
+            bool in[kPullUnroll];
 #pragma unroll
-            for (int j = 0; j < kUnroll; j++) {
+            for (int j = 0; j < kPullUnroll; j++) {
                 const OffT x = base + (OffT)(32 * j + lane_id());
                 in[j] = x < el;
                 u[j] = in[j] ? __ldg(a.in_idx + x) : 0;
             }
-            uint32_t fw[kUnroll];
+            uint32_t fw[kPullUnroll];
 #pragma unroll
-            for (int j = 0; j < kUnroll; j++) fw[j] = in[j] ? __ldcg(c.bm_cur + (u[j] >> 5)) : 0u;
+            for (int j = 0; j < kPullUnroll; j++) fw[j] = in[j] ? __ldcg(c.bm_cur + (u[j] >> 5)) : 0u;
 #pragma unroll
-            for (int j = 0; j < kUnroll; j++) {
+            for (int j = 0; j < kPullUnroll; j++) {
                 const uint32_t bal = __ballot_sync(0xffffffffu, in[j] && ((fw[j] >> (u[j] & 31)) & 1u));
                 if (bal && hit < 0) hit = __shfl_sync(0xffffffffu, u[j], __ffs(bal) - 1);
             }
-            seen += (uint32_t)min((OffT)(32 * kUnroll), el - base);
+            seen += (uint32_t)min((OffT)(32 * kPullUnroll), el - base);
         }
         if (lane_id() == l) {
             exam += seen;
@@ -600,12 +651,10 @@ __device__ __forceinline__ void pull_batch(const GraphArgs<OffT> &a, bool ok, in
     c.edges += exam;
     uint32_t cls = 0;
     if (found) {
-        const uint32_t dp = key_dist(__ldcg(a.key + par));
-        const uint2 cw = __ldg(&a.cls[(uint32_t)v >> 5]);
-        const uint32_t bit = 1u << (v & 31);
-        cls = (cw.x & bit) ? ((cw.y & bit) ? 2u : 1u) : 0u;
-        a.key[v] = ((unsigned long long)(dp + 1u) << 32) | cls;
-        atomicOr(&s_found[owner], bit);
+        const uint32_t dp = __ldcg(a.dist + par);
+        cls = class_of(a, v);
+        a.dist[v] = dp + 1u;
+        atomicOr(&s_found[owner], 1u << (v & 31));
         c.adv++;
     }
     const bool nw[1] = {found && cls != 0};
@@ -631,16 +680,16 @@ __device__ __forceinline__ void pull_words(const GraphArgs<OffT> &a, int64_t g, 
             if (left < 32) unv &= (1u << left) - 1u;
         }
     } else {
-        unsigned long long kv[kGroupWords];
+        uint32_t kv[kGroupWords];
 #pragma unroll
         for (int j = 0; j < kGroupWords; j++) {
             const int64_t v = (w0 + j) * 32 + q;
-            kv[j] = v < a.n ? __ldcg(a.key + v) : 0ull;
+            kv[j] = v < a.n ? __ldcg(a.dist + v) : 0u;
         }
 #pragma unroll
         for (int j = 0; j < kGroupWords; j++) {
             const int64_t v = (w0 + j) * 32 + q;
-            const uint32_t b = __ballot_sync(0xffffffffu, v < a.n && key_dist(kv[j]) == kInf);
+            const uint32_t b = __ballot_sync(0xffffffffu, v < a.n && kv[j] == kInf);
             if (q == j) unv = b;
         }
     }
@@ -734,7 +783,7 @@ __device__ __forceinline__ void flush_sweep(const GraphArgs<OffT> &a, SweepCtx &
 // PULL: BFS with in-arcs (llp_bfs_pull); a separate instantiation keeps the
 // pull code out of the register allocation of the push-only kernels.
 template <typename OffT, bool UNIT, bool PULL>
-__global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) {
+__global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(GraphArgs<OffT> a) {
     __shared__ BlockFlush s_flush;
     __shared__ uint32_t s_work[2];
     __shared__ uint32_t s_cwork[2];
@@ -750,6 +799,10 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
     const int warps_per_block = blockDim.x >> 5;
     const int64_t gwarp = (int64_t)blockIdx.x * warps_per_block + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
+#ifdef LLP_SWEEP_TRACE
+    __shared__ uint32_t s_first[2];
+    if (threadIdx.x == 0) s_first[1] = 0xFFFFFFFFu;
+#endif
     if (threadIdx.x == 0) {
         s_flush.marked = 0;
         s_flush.edges = 0;
@@ -775,31 +828,35 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
         const BlockCfg bcfg = block_cfg_of(c.cfg);
         c.small_max = bcfg.small_max;
         c.chunk_edges = bcfg.chunk;
+        // dense items: the widest group that still gives every warp about three items
+        c.gw = a.group_words;
+        if (c.gw != 1 && c.gw != 2 && c.gw != 4 && c.gw != kGroupWords) {
+            const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+            c.gw = kGroupWords;
+            while (c.gw > 1 && (int64_t)a.nwords / c.gw < 3 * warps) c.gw >>= 1;
+        }
     }
 
     // ---- init_global_state / initial_states_to_process (paper Sec. 3.3)
-    // four groups of 32 vertices per warp and iteration (loads in flight together)
-    for (int64_t base = gwarp * 128; base < a.n; base += nwarps * 128) {
-        uint32_t deg[4];
+    // eight groups of 32 vertices per warp and iteration (loads in flight together);
+    // a warm start keeps the caller's dist[] as the initial state
+    for (int64_t base = gwarp * 256; base < a.n; base += nwarps * 256) {
+        uint32_t deg[8];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < 8; q++) {
             const int64_t v = base + 32 * q + lane_id();
             deg[q] = v < a.n ? (uint32_t)(__ldg(a.off + v + 1) - __ldg(a.off + v)) : 0u;
         }
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < 8; q++) {
             const int64_t v = base + 32 * q + lane_id();
-            if (v < a.n) {
-                const unsigned long long cl = deg[q] == 0 ? 0ull : (deg[q] <= (uint32_t)c.small_max ? 1ull : 2ull);
-                const unsigned long long d0 =
-                    (v == a.source) ? 0ull : (a.warm ? (unsigned long long)a.dist[v] : (unsigned long long)kInf);
-                a.key[v] = (d0 << 32) | cl;
-            }
+            if (v < a.n && (!a.warm || v == a.source)) a.dist[v] = (v == a.source) ? 0u : kInf;
             const uint32_t has = __ballot_sync(0xffffffffu, deg[q] > 0);
             const uint32_t large = __ballot_sync(0xffffffffu, deg[q] > (uint32_t)c.small_max);
             if (lane_id() == 0 && base + 32 * q < a.n) {
                 const int64_t wi = (base >> 5) + q;
                 a.cls[wi] = make_uint2(has, large);
+                if (a.fixed) a.fixed[wi] = 0u;
                 a.bm[0][wi] = 0u;
                 a.bm[1][wi] = 0u;
                 a.bm[2][wi] = 0u;
@@ -833,9 +890,8 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
             uint32_t cl = 0;
             bool nw = false;
             if (u >= 0) {
-                const unsigned long long kv = __ldcg(a.key + u);
-                cl = (uint32_t)kv & 3u;
-                if (cl != 0 && key_dist(kv) != kInf) {
+                cl = class_of(a, u);
+                if (cl != 0 && __ldcg(a.dist + u) != kInf) {
                     const uint32_t bit = 1u << (u & 31);
                     nw = (atomicOr(a.bm[1] + (u >> 5), bit) & bit) == 0;
                 }
@@ -869,6 +925,7 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
     c.k = 1;
     c.fa = 0;
     c.bucket_hi = (c.delta == kInf) ? (1ull << 40) : (unsigned long long)c.delta;
+    c.fixed_lo = 0;
     uint32_t dense_sweeps = 0, pull_sweeps = 0;
     bool prev_pull = false;
     while (alive) {
@@ -933,7 +990,7 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
                 bool live = false;
                 if (ok) {
                     e = fl[i];
-                    live = key_dist(__ldcg(a.key + e.x)) == (uint32_t)e.y;
+                    live = __ldcg(a.dist + e.x) == (uint32_t)e.y;
                 }
                 bool to_near[1] = {live && (unsigned long long)(uint32_t)e.y < nh};
                 const bool keep = live && !to_near[0];
@@ -947,9 +1004,10 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
                     }
                 }
                 const int32_t vv[1] = {e.x};
-                const uint32_t cl[1] = {ok ? (uint32_t)__ldcg(a.key + e.x) & 3u : 0u};
+                const uint32_t cl[1] = {ok ? class_of(a, e.x) : 0u};
                 push_near(a, to_near, vv, cl, c);
             }
+            c.fixed_lo = c.bucket_hi;  // the bucket just emptied: everything below it is final
             c.bucket_hi = nh;
             c.fa += 1;
         } else if (PULL && c.pull) {
@@ -971,42 +1029,58 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
             // in turn from a shared counter (costs vary: skipped, partial and full chunks)
             const int2 *cl = a.chunk[k & 1];
             c.chain_on = c.chain > 0;
-            for (;;) {
-                uint32_t j = 0;
-                if (lane_id() == 0) j = atomicAdd(&s_cwork[k & 1], 1u);
-                j = __shfl_sync(0xffffffffu, j, 0);
-                const uint64_t it = (uint64_t)blockIdx.x + (uint64_t)j * gridDim.x;
-                if (it >= nc) break;
-                expand_chunk<OffT, UNIT>(a, cl[it], c);
-                if (c.chain_on) drain_local<OffT, UNIT>(a, c);
-            }
+            auto chunk_loop = [&]() {
+                for (;;) {
+                    uint32_t j = 0;
+                    if (lane_id() == 0) j = atomicAdd(&s_cwork[k & 1], 1u);
+                    j = __shfl_sync(0xffffffffu, j, 0);
+                    const uint64_t it = (uint64_t)blockIdx.x + (uint64_t)j * gridDim.x;
+                    if (it >= nc) break;
+                    expand_chunk<OffT, UNIT>(a, cl[it], c);
+                }
+            };
             // vertex groups (their cost varies): CTA b owns groups b, b + G, b + 2G, ...
             // (G = grid size) and its warps take them in turn from a shared counter
-            const uint32_t ngroups = dense ? (uint32_t)(((int64_t)a.nwords + kGroupWords - 1) / kGroupWords)
-                                           : (uint32_t)(((uint64_t)ns + 31) / 32);
-            const int32_t *sl = a.small[k & 1];
-            for (;;) {
-                uint32_t j = 0;
-                if (lane_id() == 0) j = atomicAdd(&s_work[k & 1], 1u);
-                j = __shfl_sync(0xffffffffu, j, 0);
-                const uint64_t g64 = (uint64_t)blockIdx.x + (uint64_t)j * gridDim.x;
-                if (g64 >= ngroups) break;
-                const uint32_t g = (uint32_t)g64;
-                if (dense) {
-                    scan_words<OffT, UNIT>(a, g, c);
-                    if (c.chain_on) drain_local<OffT, UNIT>(a, c);
-                } else {
-                    const int64_t i = (int64_t)g * 32 + lane_id();
-                    bool ok = i < ns;
-                    int32_t u = ok ? sl[i] : 0;
-                    if (ok) red_and(c.bm_cur + (u >> 5), ~(1u << (u & 31)));
-                    expand_group<OffT, UNIT>(a, ok, u, c, c.bm_next);  // advanced again: next sweep
-                    if (c.chain_on) drain_local<OffT, UNIT>(a, c);
+            auto group_loop = [&]() {
+                const uint32_t ngroups = dense ? (uint32_t)(((int64_t)a.nwords + c.gw - 1) / c.gw)
+                                               : (uint32_t)(((uint64_t)ns + 31) / 32);
+                const int32_t *sl = a.small[k & 1];
+                for (;;) {
+                    uint32_t j = 0;
+                    if (lane_id() == 0) j = atomicAdd(&s_work[k & 1], 1u);
+                    j = __shfl_sync(0xffffffffu, j, 0);
+                    const uint64_t g64 = (uint64_t)blockIdx.x + (uint64_t)j * gridDim.x;
+                    if (g64 >= ngroups) break;
+                    const uint32_t g = (uint32_t)g64;
+                    if (dense) {
+                        scan_words<OffT, UNIT>(a, g, c);
+                        if (c.chain_on) drain_local<OffT, UNIT>(a, c);
+                    } else {
+                        const int64_t i = (int64_t)g * 32 + lane_id();
+                        bool ok = i < ns;
+                        int32_t u = ok ? sl[i] : 0;
+                        if (ok) red_and(c.bm_cur + (u >> 5), ~(1u << (u & 31)));
+                        expand_group<OffT, UNIT>(a, ok, u, c, c.bm_next);  // advanced again: next sweep
+                        if (c.chain_on) drain_local<OffT, UNIT>(a, c);
+                    }
                 }
-            }
+            };
+            chunk_loop();
+            group_loop();
             c.chain_on = false;
         }
+#ifdef LLP_SWEEP_TRACE
+        // s_first[k & 1] was reset during sweep k - 1 (a grid barrier separates the two)
+        if (threadIdx.x == 0) s_first[(k + 1) & 1] = 0xFFFFFFFFu;
+        if (lane_id() == 0) atomicMin(&s_first[k & 1], (uint32_t)(globaltimer_ns() - t0));
+#endif
         flush_sweep(a, c, &s_flush);
+#ifdef LLP_SWEEP_TRACE
+        if (threadIdx.x == 0 && k - 1 < 64 && blockIdx.x < 1024) {
+            a.trace[((k - 1) * 1024 + blockIdx.x) * 2] = s_first[k & 1];
+            a.trace[((k - 1) * 1024 + blockIdx.x) * 2 + 1] = (uint32_t)(globaltimer_ns() - t0);
+        }
+#endif
         prev_pull = c.pull;
         c.vis_valid = c.pull;  // push sweeps reach vertices without recording them in vis
         c.pull = false;
@@ -1014,8 +1088,7 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
         c.k += 1;
     }
 
-    // ---- final_solution: dist[v] = d(v)
-    for (int64_t v = gtid; v < a.n; v += gthreads) a.dist[v] = key_dist(__ldcg(a.key + v));
+    // ---- final_solution: dist[] already holds G
 
     // ---- statistics (one atomic per warp)
     const unsigned long long it_s = warp_sum(c.items), ed_s = warp_sum(c.edges), ad_s = warp_sum(c.adv);
@@ -1038,14 +1111,16 @@ __global__ void __launch_bounds__(512, 2) graph_sweep_kernel(GraphArgs<OffT> a) 
 }
 
 struct Layout {
-    unsigned long long *key;
     uint2 *cls;
     uint32_t *bm[3];
     uint32_t *vis;
+    uint32_t *fixed;
     int32_t *small[2];
     int2 *chunk[2];
     int2 *far[2];
     uint32_t far_cap;
+    uint32_t *trace;
+    void *lb_lists;  // the load-balanced engine's lists (they overlay the lists above)
     size_t bytes;
 };
 
@@ -1056,18 +1131,28 @@ Layout carve_graph(void *ws, int32_t n, int64_t m) {
     // chunks of one sweep: sum over large v of ceil(deg/chunk) <= m/128 + m/17
     const size_t chunk_cap = (size_t)(m / 128 + m / 16 + 2);
     L.far_cap = (uint32_t)std::max<int64_t>(n, 1024);
-    L.key = c.take<unsigned long long>(n);
     L.cls = c.take<uint2>(nwords);
     L.bm[0] = c.take<uint32_t>(nwords);
     L.bm[1] = c.take<uint32_t>(nwords);
     L.bm[2] = c.take<uint32_t>(nwords);
     L.vis = c.take<uint32_t>(nwords);
+    L.fixed = c.take<uint32_t>(nwords);
+    const size_t lists_at = c.off;
     L.small[0] = c.take<int32_t>(n);
     L.small[1] = c.take<int32_t>(n);
     L.chunk[0] = c.take<int2>(chunk_cap);
     L.chunk[1] = c.take<int2>(chunk_cap);
     L.far[0] = c.take<int2>(L.far_cap);
     L.far[1] = c.take<int2>(L.far_cap);
+    // the load-balanced engine's lists overlay the lists above (one engine per call)
+    const size_t lists_at_al = align_up(lists_at, 256);
+    L.lb_lists = ws ? (void *)((char *)ws + lists_at_al) : nullptr;
+    c.off = std::max(c.off, lists_at_al + lb_workspace_bytes(n, m));
+#ifdef LLP_SWEEP_TRACE
+    L.trace = c.take<uint32_t>(64 * 1024 * 2);
+#else
+    L.trace = nullptr;
+#endif
     L.bytes = c.bytes();
     return L;
 }
@@ -1124,6 +1209,15 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         if (rc != LLP_OK) return rc;
     }
 
+    // Block configuration 4 selects the load-balanced engine (lb_sweep.cu): one worklist (no
+    // buckets), no local chain, no pull sweeps, the schedule chosen on the host, int32 offsets.
+    const int lchain = (s && s->local_chain > 0) ? s->local_chain : 0;
+    const bool lb_ok = s && s->block_cfg == 4 && !learned && !pull_on && !g->offsets_64 && delta == kInf &&
+                       lchain == 0;
+    if (lb_ok) {
+        return lb_launch(UNIT, g, source, out, L.bm[0], L.bm[1], L.lb_lists, (WsHeader *)ws, deadline_from(s), mode,
+                         dense_arcs, seeds, n_seeds, stream);
+    }
     // Grid size: small graphs sweep faster on fewer CTAs (their sweeps are short chains of
     // dependent loads plus a grid barrier whose cost grows with the CTA count); one CTA per
     // 1,024 vertices, at least 32, at most every co-resident CTA.
@@ -1135,7 +1229,6 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         args.w = UNIT ? nullptr : g->weights;
         args.dist = out;
         args.nwords = (int32_t)(((int64_t)g->n + 31) / 32);
-        args.key = L.key;
         args.cls = L.cls;
         args.bm[0] = L.bm[0];
         args.bm[1] = L.bm[1];
@@ -1150,6 +1243,8 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         args.far[0] = L.far[0];
         args.far[1] = L.far[1];
         args.far_cap = L.far_cap;
+        args.trace = L.trace;
+        args.fixed = (!UNIT && s && s->fixed_memo > 0 && delta != kInf) ? L.fixed : nullptr;
         args.h = (WsHeader *)ws;
         args.delta = delta;
         args.mode = mode;
@@ -1159,6 +1254,7 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         args.cfg = cfg;
         args.use_dev_sched = learned ? 1 : 0;
         args.local_chain = (s && s->local_chain > 0) ? s->local_chain : 0;
+        args.group_words = s ? s->group_words : 0;
         args.deadline_ns = deadline_from(s);
         args.warm = n_seeds >= 0 ? 1 : 0;
         args.n_seeds = n_seeds > 0 ? n_seeds : 0;

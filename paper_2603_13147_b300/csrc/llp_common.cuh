@@ -59,6 +59,8 @@ struct alignas(256) WsHeader {
     // [0] CTAs finished (t_end), [1..2] closure change flags, [7] pull sweeps,
     // [8] local chain used, [9..14] feature accumulators, [15] feature CTAs finished
     uint32_t scratch[16];
+    // load-balanced engine: per list (sweep k uses k % 3) entries << 32 | arcs
+    unsigned long long lb_cursor[3];
     // ---- schedule chosen on the device by the learned scheduler (graph engine)
     int32_t sched_mode;
     uint32_t sched_delta;

@@ -125,9 +125,12 @@ def test_batch_full_config_sampled(llp):
     assert st["status"] == 0, st
     assert st["items"] == 4096 + 2048 + 1024
     rng = np.random.default_rng(0)
-    check_knap(db, knap, rng.choice(4096, 12, replace=False))
-    check_job(db, job, rng.choice(2048, 64, replace=False))
-    check_sm(db, sm, rng.choice(1024, 48, replace=False))
+    cells = np.diff(knap["item_off"]) * (knap["capacity"].astype(np.int64) + 1)
+    largest = np.argsort(cells)[-4:]  # the biggest n * W instances, then a seeded sample
+    check_knap(db, knap, np.unique(np.concatenate([largest, rng.choice(4096, 60, replace=False)])))
+    jobs = np.diff(job["job_off"])
+    check_job(db, job, np.unique(np.concatenate([np.argsort(jobs)[-4:], rng.choice(2048, 64, replace=False)])))
+    check_sm(db, sm, np.unique(np.concatenate([np.argsort(sm["n"])[-4:], rng.choice(1024, 48, replace=False)])))
 
 
 # ----------------------------------------------------- small SSSP / BFS family

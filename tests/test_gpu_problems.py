@@ -87,6 +87,31 @@ def test_knapsack(llp, n, W, seed):
     assert (row.cpu().numpy() == rrow).all()
 
 
+@pytest.mark.parametrize("n,W,seed,cfg", [(2048, 65536, 5, 1), (1000, 30000, 8, 0), (1001, 65536, 9, 0),
+                                          (2000, 200000, 10, 0), (4096, 4096, 11, 0), (3, 100000, 12, 0)])
+def test_knapsack_cluster_and_single_cta(llp, n, W, seed, cfg):
+    """Large instances run on a thread-block cluster (rows in distributed shared memory, three
+    items per pass: ragged item counts leave a partial last pass); block_cfg 1 forces the one-CTA
+    kernel on the same instance."""
+    w, v = synth.knapsack(n, W, seed=seed)
+    best, row, ws = llp.knapsack(T(w), T(v), W, sched=llp.make_sched(block_cfg=cfg))
+    assert llp.get_status(ws)["status"] == 0
+    rb, rrow = oracle.knapsack(w, v, W)
+    assert int(best.item()) == rb
+    assert (row.cpu().numpy() == rrow).all()
+
+
+def test_knapsack_cluster_invalid_item_reported(llp):
+    """An item outside the problem statement (weight 0) is skipped and reported on the cluster path."""
+    w, v = synth.knapsack(2048, 65536, seed=13)
+    w[100] = 0
+    best, row, ws = llp.knapsack(T(w), T(v), 65536)
+    assert llp.get_status(ws)["status"] == llp.LLP_ERR_INVALID_ARG
+    keep = np.ones(2048, bool)
+    keep[100] = False
+    assert int(best.item()) == oracle.knapsack(w[keep], v[keep], 65536)[0]
+
+
 def test_knapsack_overflow_reported(llp):
     w = np.ones(4, np.int32)
     v = np.full(4, 0x7FFFFFFF // 3, np.int32)
@@ -109,8 +134,9 @@ def test_job_paper_example(llp):
     assert c.cpu().numpy().tolist() == [int(x) for x in gd["completion"][0].split()]
 
 
-@pytest.mark.parametrize("n,seed", [(1, 0), (64, 1), (5000, 2), (8192, 3), (200000, 4)])
+@pytest.mark.parametrize("n,seed", [(1, 0), (64, 1), (5000, 2), (8192, 3), (200000, 4), (1 << 20, 5)])
 def test_job_random(llp, n, seed):
+    """Random job DAGs up to the benchmarked 1,048,576-job DAG (the same seed)."""
     g, dur = synth.job_dag(n, seed=seed)
     c, ws = llp.job_schedule(job_dev(llp, g), T(dur))
     st = llp.get_status(ws)
