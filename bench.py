@@ -628,7 +628,12 @@ def bench_batched(llp, dev, stream, div=1, cpu=True):
             "plain_sample": "every 16th knapsack, 8th job DAG and 8th marriage instance, scaled",
             "plain_sampling_rel_err": {f: abs(e[0] - e[1]) / (e[0] + e[1]) for f, e in
                                        (("knapsack", ek), ("job", ej), ("marriage", es))},
-            "cfg": {"threads": cfg.threads, "knap_unroll": cfg.knap_unroll}, "autotune_ms": tune_ms,
+            "cfg": {"threads": cfg.threads, "knap_unroll": cfg.knap_unroll, "ctas_per_sm": cfg.ctas_per_sm},
+            "autotune": {"candidates": [{"threads": t, "ctas_per_sm": c, "knap_unroll": u, "ms": ms}
+                                        for (t, c, u), ms in zip([(t, c, u) for t, c in ((1024, 1), (512, 1), (512, 2),
+                                                                                          (256, 2)) for u in (4, 8, 16)],
+                                                                 tune_ms)]},
+            "autotune_ms": tune_ms,
             "status": bst["status"], "cuda_graph": True, "knapsack_roofline": knap_roof,
             "cpu_baseline": cpu_base}
 

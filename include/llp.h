@@ -381,7 +381,10 @@ typedef struct llp_batch {
 typedef struct llp_batch_cfg {
     int32_t threads;     /* threads per CTA: 256, 512 or 1024 (default 1024) */
     int32_t knap_unroll; /* knapsack cells per thread per chunk: 4, 8 (default) or 16 */
-    int32_t reserved[2];
+    int32_t ctas_per_sm; /* resident CTAs per SM: 1 (default) or 2 (threads <= 512; each CTA then has
+                            half the shared memory, so larger instances keep their state in the
+                            per-CTA global scratch) */
+    int32_t reserved;
 } llp_batch_cfg_t;
 
 size_t llp_batch_workspace_size(const llp_batch_t *b);
@@ -389,7 +392,8 @@ llp_status_t llp_batch_solve(const llp_batch_t *b, const llp_batch_cfg_t *cfg, c
                              size_t ws_bytes, void *stream);
 
 /* Autotuner: runs the batch once untimed and once timed (CUDA events) for every
- * candidate launch shape and writes the fastest to *best.  Synchronises
+ * candidate launch shape (threads 1024/512 at one CTA per SM, 512/256 at two, each
+ * with knapsack blocking 4, 8, 16: 12 candidates) and writes the fastest to *best.  Synchronises
  * `stream`.  h_ms (may be NULL) receives up to max_tried timings; *n_tried the
  * number of candidates run.  Outputs of the batch hold the last run's result. */
 llp_status_t llp_batch_autotune(const llp_batch_t *b, void *ws, size_t ws_bytes, void *stream,

@@ -464,7 +464,8 @@ class Batch(ctypes.Structure):
 
 
 class BatchCfg(ctypes.Structure):
-    _fields_ = [("threads", ctypes.c_int32), ("knap_unroll", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+    _fields_ = [("threads", ctypes.c_int32), ("knap_unroll", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class DeviceBatch:

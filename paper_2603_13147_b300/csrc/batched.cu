@@ -215,9 +215,10 @@ int max_dyn_smem() {
     return lim - 1024;
 }
 
-BatchPlan plan_batch(const llp_batch_t *b) {
+// ctas: resident CTAs per SM (1 or 2); each gets 1/ctas of the shared memory.
+BatchPlan plan_batch(const llp_batch_t *b, int ctas = 1) {
     BatchPlan p{};
-    p.smem_bytes = (size_t)max_dyn_smem() / 16 * 16;
+    p.smem_bytes = (size_t)max_dyn_smem() / ctas / 16 * 16;
     size_t need = 0;
     if (b->knap_count > 0 && (size_t)(b->knap_max_capacity + 1) * 4 > p.smem_bytes)
         need = std::max(need, (size_t)(b->knap_max_capacity + 1) * 4);
@@ -229,7 +230,7 @@ BatchPlan plan_batch(const llp_batch_t *b) {
     }
     p.cta_scratch_bytes = align_up(need, 256);
     const DeviceInfo di = device_info();
-    p.grid_max = (di.sms > 0 ? di.sms : 148);
+    p.grid_max = (di.sms > 0 ? di.sms : 148) * ctas;
     const size_t total = (size_t)b->knap_count + b->job_count + b->sm_count + b->gr_count;
     Carve c(nullptr);
     c.take<uint32_t>(total);
@@ -274,7 +275,8 @@ extern "C" {
 
 size_t llp_batch_workspace_size(const llp_batch_t *b) {
     if (llp::validate_batch(b) != LLP_OK) return 0;
-    return llp::plan_batch(b).total_bytes;
+    // enough for either launch shape (two CTAs per SM have more, smaller scratch areas)
+    return std::max(llp::plan_batch(b, 1).total_bytes, llp::plan_batch(b, 2).total_bytes);
 }
 
 llp_status_t llp_batch_solve(const llp_batch_t *b, const llp_batch_cfg_t *cfg, const llp_sched_t *sched, void *ws,
@@ -283,10 +285,12 @@ llp_status_t llp_batch_solve(const llp_batch_t *b, const llp_batch_cfg_t *cfg, c
     llp_status_t rc = validate_batch(b);
     if (rc != LLP_OK) return rc;
     if (!ws || ((uintptr_t)ws & 255u) != 0) return LLP_ERR_INVALID_ARG;
-    const BatchPlan p = plan_batch(b);
+    int threads = (cfg && (cfg->threads == 256 || cfg->threads == 512 || cfg->threads == 1024))
+                      ? cfg->threads : 1024;
+    const int ctas = (cfg && cfg->ctas_per_sm == 2) ? 2 : 1;
+    if (ctas == 2 && threads > 512) threads = 512;
+    const BatchPlan p = plan_batch(b, ctas);
     if (ws_bytes < p.total_bytes) return LLP_ERR_WORKSPACE_TOO_SMALL;
-    const int threads = (cfg && (cfg->threads == 256 || cfg->threads == 512 || cfg->threads == 1024))
-                            ? cfg->threads : 1024;
     const int unroll = (cfg && (cfg->knap_unroll == 4 || cfg->knap_unroll == 16)) ? cfg->knap_unroll : 8;
     cudaStream_t st = (cudaStream_t)stream;
     rc = reset_header(ws, st);
@@ -313,7 +317,8 @@ llp_status_t llp_batch_autotune(const llp_batch_t *b, void *ws, size_t ws_bytes,
                                 llp_batch_cfg_t *best, float *h_ms, int32_t max_tried, int32_t *n_tried) {
     using namespace llp;
     if (!best) return LLP_ERR_INVALID_ARG;
-    static const int kThreads[] = {512, 1024};
+    // (threads, CTAs per SM) x knapsack blocking
+    static const int kShape[][2] = {{1024, 1}, {512, 1}, {512, 2}, {256, 2}};
     static const int kUnrollC[] = {4, 8, 16};
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
@@ -325,10 +330,11 @@ llp_status_t llp_batch_autotune(const llp_batch_t *b, void *ws, size_t ws_bytes,
     float best_ms = 1e30f;
     int tried = 0;
     llp_status_t rc = LLP_OK;
-    for (int t : kThreads)
+    for (const auto &sh : kShape)
         for (int u : kUnrollC) {
             llp_batch_cfg_t c{};
-            c.threads = t;
+            c.threads = sh[0];
+            c.ctas_per_sm = sh[1];
             c.knap_unroll = u;
             // one untimed run (warm), one timed run
             rc = llp_batch_solve(b, &c, nullptr, ws, ws_bytes, stream);

@@ -135,16 +135,17 @@ __global__ void __launch_bounds__(kClusterThreads) knapsack_cluster(int32_t n, c
             for (int q = 0; q < kClusterCells; q++) {
                 const int32_t c = lo + i0 + q * T + tid;
                 const bool live = i0 + q * T + tid < S && c <= W;
+                // every term is loaded (a term that does not fit reads the cell itself and is
+                // dropped below), so all the loads of a cell group can be in flight together
+                const int32_t cc = live ? c : lo;
                 int32_t val[NS];
 #pragma unroll
                 for (int m = 0; m < NS; m++) {
-                    val[m] = 0;
-                    if (live && ws[m] <= c) {
-                        const uint32_t x = (uint32_t)(c - ws[m]);
-                        uint32_t r = __umulhi(x, inv_s);
-                        if (r * (uint32_t)S > x) r--;
-                        val[m] = ld_cluster(cluster_addr(src_sh + 4u * (x - r * (uint32_t)S), r)) + vs[m];
-                    }
+                    const bool fits = ws[m] <= cc;
+                    const uint32_t x = (uint32_t)(fits ? cc - ws[m] : cc);
+                    uint32_t r = __umulhi(x, inv_s);
+                    if (r * (uint32_t)S > x) r--;
+                    val[m] = ld_cluster(cluster_addr(src_sh + 4u * (x - r * (uint32_t)S), r)) + (fits ? vs[m] : 0);
                 }
                 b[q] = val[0];
 #pragma unroll

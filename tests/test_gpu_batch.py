@@ -57,12 +57,12 @@ def check_sm(db, sm, idx):
         assert (wife[mo[i]:mo[i + 1]] == oracle.stable_marriage(mp, wr)[0]).all(), i
 
 
-@pytest.mark.parametrize("threads,unroll", [(1024, 8), (512, 4), (256, 16)])
-def test_batch_small_all_instances(llp, threads, unroll):
-    knap, job, sm = small_batches(seed=threads)
+@pytest.mark.parametrize("threads,unroll,ctas", [(1024, 8, 1), (512, 4, 1), (256, 16, 1), (512, 8, 2), (256, 4, 2)])
+def test_batch_small_all_instances(llp, threads, unroll, ctas):
+    knap, job, sm = small_batches(seed=threads + ctas)
     db = llp.DeviceBatch(knap, job, sm)
     cfg = llp.BatchCfg()
-    cfg.threads, cfg.knap_unroll = threads, unroll
+    cfg.threads, cfg.knap_unroll, cfg.ctas_per_sm = threads, unroll, ctas
     ws = llp.batch_solve(db, cfg)
     st = llp.get_status(ws)
     assert st["status"] == 0, st
@@ -107,7 +107,8 @@ def test_batch_autotune_picks_a_candidate(llp):
     knap, job, sm = small_batches(seed=9, kc=30, jc=10, sc=10)
     db = llp.DeviceBatch(knap, job, sm)
     best, ms, ws = llp.batch_autotune(db)
-    assert len(ms) == 6 and best.threads in (512, 1024) and best.knap_unroll in (4, 8, 16)
+    assert len(ms) == 12 and best.threads in (256, 512, 1024) and best.knap_unroll in (4, 8, 16)
+    assert best.ctas_per_sm in (1, 2)
     assert min(ms) > 0
     check_knap(db, knap, range(knap["count"]))
 
@@ -150,13 +151,13 @@ def check_graphs(db, gb, idx):
         assert (dist[v0:v1] == ref).all(), i
 
 
-@pytest.mark.parametrize("threads,unroll", [(1024, 8), (512, 4), (256, 16)])
-def test_batch_graphs_with_other_families(llp, threads, unroll):
+@pytest.mark.parametrize("threads,unroll,ctas", [(1024, 8, 1), (512, 4, 1), (256, 16, 1), (512, 16, 2)])
+def test_batch_graphs_with_other_families(llp, threads, unroll, ctas):
     knap, job, sm = small_batches(seed=threads + 1, kc=10, jc=10, sc=10)
     gb = synth.graph_batch(48, 1, 4000, seed=threads)
     db = llp.DeviceBatch(knap, job, sm, gb)
     cfg = llp.BatchCfg()
-    cfg.threads, cfg.knap_unroll = threads, unroll
+    cfg.threads, cfg.knap_unroll, cfg.ctas_per_sm = threads, unroll, ctas
     ws = llp.batch_solve(db, cfg)
     st = llp.get_status(ws)
     assert st["status"] == 0, st

@@ -54,7 +54,11 @@ def csr_from_arcs(n, arcs):
 SCHEDS = [dict(), dict(mode=1), dict(mode=2), dict(mode=1, delta=64), dict(mode=0, delta=8, block_cfg=1),
           dict(mode=2, delta=300, block_cfg=3, threads=256), dict(delta=1, block_cfg=1),
           dict(mode=1, local_chain=4), dict(mode=2, local_chain=16, delta=500), dict(local_chain=64, block_cfg=3),
-          dict(mode=1, local_chain=1, delta=1, threads=256)]
+          dict(mode=1, local_chain=1, delta=1, threads=256),
+          # dense-sweep group widths; fixed-state memoization (needs buckets); the load-balanced engine
+          dict(group_words=1), dict(mode=2, group_words=2, block_cfg=1), dict(group_words=4, delta=64, fixed_memo=1),
+          dict(mode=1, delta=8, fixed_memo=1), dict(mode=2, delta=300, fixed_memo=1, local_chain=4),
+          dict(block_cfg=4), dict(block_cfg=4, mode=1), dict(block_cfg=4, mode=2, threads=256)]
 
 
 def test_paper_example(llp):
@@ -113,7 +117,9 @@ def test_random_small_and_ragged(llp, seed):
     assert (d == refb).all()
 
 
-@pytest.mark.parametrize("kw", [dict(), dict(mode=1, local_chain=16), dict(mode=2, local_chain=4, delta=2000)])
+@pytest.mark.parametrize("kw", [dict(), dict(mode=1, local_chain=16), dict(mode=2, local_chain=4, delta=2000),
+                                dict(mode=2, local_chain=4, delta=2000, fixed_memo=1), dict(delta=500, fixed_memo=1),
+                                dict(block_cfg=4), dict(group_words=8)])
 def test_grid_graph_schedules(llp, kw):
     """Road-like input (2-D grid, both arc directions): long paths, thousands of sweeps."""
     g = synth.grid_graph(96, 77, 1, 1000, seed=5)
@@ -192,6 +198,10 @@ def test_rmat22_sssp_full(llp, rmat22):
     ref = oracle.sssp(g["offsets"], g["indices"], g["weights"], s)
     d, st = run_sssp(llp, g, s)
     assert (d == ref).all()
+    # the load-balanced engine and fixed-state memoization (with buckets) on the same graph
+    for kw in (dict(block_cfg=4), dict(delta=512, fixed_memo=1)):
+        d, _ = run_sssp(llp, g, s, **kw)
+        assert (d == ref).all(), kw
 
 
 def test_rmat22_bfs_full(llp, rmat22):
@@ -387,7 +397,8 @@ def run_warm(llp, g, s, d_old, seeds, unit=False, **kw):
 
 
 @pytest.mark.parametrize("kw", [dict(), dict(mode=1, delta=64), dict(mode=2), dict(mode=1, local_chain=16),
-                                dict(delta=300, block_cfg=3, threads=256)])
+                                dict(delta=300, block_cfg=3, threads=256), dict(block_cfg=4),
+                                dict(block_cfg=4, mode=2), dict(delta=64, fixed_memo=1)])
 def test_warm_er16k(llp, kw):
     g = synth.er16k()
     rng = np.random.default_rng(31)
