@@ -279,6 +279,20 @@ def run_gpu(args):
     if kernel_src_sha() == TRAFFIC_CAPTURE["src_sha"]:
         traffic = int(TRAFFIC_CAPTURE["bytes_per_alg_byte"] * alg_bytes)
 
+    # access-pattern floor of a push sweep on this graph: one pass over all m arcs, CSR
+    # streamed, one random read of per-vertex state per arc (llp_gather_floor), same protocol
+    sink = llp.gather_floor(dg, dist_t)
+    torch.cuda.synchronize(dev)
+    fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        fev[i][0].record(stream)
+        llp.gather_floor(dg, dist_t, sink=sink)
+        fev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    floor_ms = float(np.mean([a.elapsed_time(b) for a, b in fev]))
+    del sink
+
     # BFS on the same graph (reported beside the headline)
     for _ in range(2):
         llp.bfs(dg, s, out=dist_t, ws=ws)
@@ -395,7 +409,13 @@ def run_gpu(args):
                    "schedule": {k: st[k] for k in ("mode_used", "delta_used", "block_cfg_used")}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "traffic_note": "scaled from an R-MAT scale 20 capture by algorithmic bytes", "peak_kind": peak_kind, "frac_of_nominal_8tbs": achieved / 8000.0,
-                     "alg_bytes_per_launch": alg_bytes, "kernel": "graph_sweep_kernel<int32,false>"},
+                     "alg_bytes_per_launch": alg_bytes, "kernel": "graph_sweep_kernel<int32,false>",
+                     "gather_floor_ms": floor_ms,
+                     "gather_floor_note": "llp_gather_floor: one pass over all m arcs, CSR streamed with 16-byte "
+                                          "loads, one random read of per-vertex state per arc, 8 in flight per lane",
+                     "gather_floor_g_arcs_per_s": g.m / (floor_ms * 1e-3) / 1e9,
+                     "sweep_g_arcs_per_s": st["edges"] / (ms * 1e-3) / 1e9,
+                     "floor_for_arcs_examined_ms": floor_ms * st["edges"] / g.m},
         "sweep_stats": {"sweeps": st["sweeps"], "edges_scanned": st["edges"], "advances": st["advances"],
                         "dense_sweeps": st["dense_sweeps"], "edges_per_reached_arc": st["edges"] / max(mr, 1),
                         "device_loop_ms": st["elapsed_ns"] / 1e6,

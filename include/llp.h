@@ -225,6 +225,17 @@ llp_status_t llp_sssp_noalloc(const llp_csr_t *g, int32_t source, uint32_t *dist
  * is NULL. */
 llp_status_t llp_sssp_noalloc_status(int32_t *status, void *stream);
 
+/* Measurement helper with no counterpart in the paper: the access-pattern floor of
+ * a push sweep.  One pass over all m arcs of g that streams indices[] and
+ * weights[] (16-byte loads; both arrays 16-byte aligned) and reads state[v] at
+ * random for every arc's target v (state: n uint32 values, any contents), with
+ * 8 reads per lane in flight.  Its device time is the time any push sweep needs
+ * to touch every arc once; the benchmark reports it beside the sweep kernel's.
+ * sink: llp_gather_floor_sink_size() bytes of device memory, overwritten.
+ * Stream-ordered; allocates nothing. */
+size_t llp_gather_floor_sink_size(void);
+llp_status_t llp_gather_floor(const llp_csr_t *g, const uint32_t *state, void *sink, size_t sink_bytes, void *stream);
+
 /* ------------------------------------------------------------------- BFS
  * Paper Sec. 4.2: G[v] = level; v is forbidden iff an in-neighbour u has
  * G[u] < G[v] - 1; advance sets G[v] = 1 + min G[u].  level[v] = hop distance

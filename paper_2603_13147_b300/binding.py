@@ -409,6 +409,21 @@ def sweep_log(ws: torch.Tensor, stream=None, max_records: int = 4096):
     return buf[:cnt]
 
 
+def gather_floor(g: DeviceGraph, state: torch.Tensor, sink: torch.Tensor | None = None, stream=None):
+    """The access-pattern floor of a push sweep: one pass over every arc of g that streams the CSR
+    and reads state[target] at random (llp_gather_floor).  Returns the sink tensor (reuse it)."""
+    L = lib()
+    L.llp_gather_floor_sink_size.restype = ctypes.c_size_t
+    nbytes = int(L.llp_gather_floor_sink_size())
+    if sink is None:
+        sink = torch.empty(nbytes, dtype=torch.uint8, device=g.indices.device)
+    _dev(state, torch.int32, "state")
+    c = g.csr()
+    rc = L.llp_gather_floor(ctypes.byref(c), _ptr(state), _ptr(sink), ctypes.c_size_t(sink.numel()), _stream(stream))
+    _check(rc, "llp_gather_floor")
+    return sink
+
+
 def sssp_noalloc_max_workspace() -> int:
     L = lib()
     L.llp_sssp_noalloc_max_workspace.restype = ctypes.c_size_t

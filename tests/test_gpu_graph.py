@@ -497,3 +497,25 @@ def test_stats_report_the_schedule_used(llp):
     assert (d == ref).all()
     assert st["mode_used"] == 2 and st["local_chain_used"] == 0 and st["delta_used"] == llp.DELTA_INF
     assert st["dense_sweeps"] == st["sweeps"] - 2  # all but the first (list) and the last (empty) sweep
+
+
+@pytest.mark.parametrize("m_extra", [0, 1, 3])
+def test_gather_floor_reads_every_arc(llp, m_extra):
+    """The access-pattern floor pass touches every arc once: the minimum over its per-thread
+    results is min over arcs of state[target] + weight (vector body and the ragged tail)."""
+    g = synth.er_graph(5000, 40000 + m_extra, 1, 100, seed=4)
+    dg = dev_graph(llp, g)
+    rng = np.random.default_rng(1)
+    state = rng.integers(0, 1 << 20, g["n"]).astype(np.int32)
+    sink = llp.gather_floor(dg, torch.from_numpy(state).cuda())
+    got = int(sink.view(torch.int64).cpu().numpy().view(np.uint64).min())
+    want = int((state[g["indices"]].astype(np.uint64) + g["weights"].astype(np.uint64)).min())
+    assert got == want
+    # one target made cheap at a time: the first arc, a middle one and the last (the tail)
+    for e in (0, g["m"] // 2, g["m"] - 1):
+        st2 = np.full(g["n"], 1 << 30, np.int32)
+        v = g["indices"][e]
+        st2[v] = 0
+        sink = llp.gather_floor(dg, torch.from_numpy(st2).cuda(), sink=sink)
+        got = int(sink.view(torch.int64).cpu().numpy().view(np.uint64).min())
+        assert got == int(g["weights"][g["indices"] == v].min()), e
