@@ -843,22 +843,15 @@ def bench_learned(llp, dev, g22, s22, cpu=True, cpu22_s=None):
         t_search = time.perf_counter() - t_search
         asch = S.label_to_sched(label, wmax)
         ta = _ev_time(lambda: llp.sssp(dg, src, out=out, ws=ws, sched=asch), reps=3)
-        gw_best = 0
-        for gw in (1, 2, 4, 8):  # the dense-sweep group width, a fifth coordinate
-            asch.group_words = gw
-            tg = _ev_time(lambda: llp.sssp(dg, src, out=out, ws=ws, sched=asch), reps=3)
-            if tg < ta * 0.97:
-                ta, gw_best = tg, gw
-        asch.group_words = gw_best
-        ta = _ev_time(lambda: llp.sssp(dg, src, out=out, ws=ws, sched=asch), reps=3)
         same_a = bool(torch.equal(ref, out))
         ent = {"heuristic_ms": th, "learned_ms": tl, "autotuned_ms": ta,
                "learned_schedule": [st["mode_used"], st["delta_used"], st["block_cfg_used"],
                                     st["local_chain_used"]],
+               "learned_schedule_fields": ["mode", "delta", "block_cfg", "local_chain"],
                "autotuned_schedule": {"mode": int(label[0]), "delta": S.delta_of_class(int(label[1]), wmax),
                                       "block_cfg": int(label[2]) + 1,
                                       "local_chain": S.CHAIN_OF_CLASS[int(label[3])],
-                                      "group_words": gw_best},
+                                      "group_words": S.GW_OF_CLASS[int(label[4])]},
                "autotune_candidates": len(log), "autotune_search_s": t_search,
                "bit_exact": same_l and same_a}
         if cpu:

@@ -416,10 +416,11 @@ llp_status_t llp_batch_autotune(const llp_batch_t *b, void *ws, size_t ws_bytes,
  * of the graph sweep.  Setting llp_sched_t.use_mlp = 1 and mlp_params makes
  * llp_sssp / llp_bfs run a feature kernel and an inference kernel on the device
  * before the sweep, which then uses the chosen schedule.  Results never depend
- * on the schedule.  The scheduler network is features(16) -> 64 -> 64 -> 18
+ * on the schedule.  The scheduler network is features(16) -> 64 -> 64 -> 23
  * logits = heads {mode: 3 (AUTO, SPARSE, DENSE), bucket-width class: 8
  * (0 = none, c >= 1: width = max sampled weight * 2^(c-1)), block_cfg: 3,
- * local chain: 4 (off, 4, 16, 64 batches)}.
+ * local chain: 4 (off, 4, 16, 64 batches), dense-sweep group width: 5 (the
+ * grid-size rule, 1, 2, 4, 8 words)}.
  * Parameters: one fp32 vector, row-major W1[F,H1] b1 W2[H1,H2] b2 W3[H2,O] b3. */
 typedef struct llp_mlp_dims {
     int32_t F, H1, H2, O; /* each 1..128 */

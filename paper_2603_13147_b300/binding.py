@@ -584,7 +584,7 @@ class MlpDims(ctypes.Structure):
 
 
 SCHED_F, SCHED_H1, SCHED_H2 = 16, 64, 64
-SCHED_HEADS = (3, 8, 3, 4)  # mode, bucket-width class, block_cfg, local-chain class
+SCHED_HEADS = (3, 8, 3, 4, 5)  # mode, bucket-width class, block_cfg, local-chain class, group-width class
 
 
 def mlp_dims(F=SCHED_F, H1=SCHED_H1, H2=SCHED_H2, heads=SCHED_HEADS) -> MlpDims:

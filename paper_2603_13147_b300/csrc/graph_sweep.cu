@@ -824,12 +824,14 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
         if (c.cfg < 1 || c.cfg > LLP_BLOCK_CFGS) c.cfg = 2;
         if (UNIT) c.delta = kInf;
     }
+    int32_t gw_req = a.group_words;
+    if (a.use_dev_sched && *(volatile int32_t *)&h->sched_valid) gw_req = *(volatile int32_t *)&h->sched_gw;
     {
         const BlockCfg bcfg = block_cfg_of(c.cfg);
         c.small_max = bcfg.small_max;
         c.chunk_edges = bcfg.chunk;
         // dense items: the widest group that still gives every warp about three items
-        c.gw = a.group_words;
+        c.gw = gw_req;
         if (c.gw != 1 && c.gw != 2 && c.gw != 4 && c.gw != kGroupWords) {
             const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
             c.gw = kGroupWords;

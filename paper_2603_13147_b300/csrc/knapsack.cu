@@ -16,7 +16,8 @@
 // pass applies K items at once: G[k+K-1, c] = max over the subsets T of the K
 // items that fit of G[k-1, c - w(T)] + v(T) (the recurrence unrolled K times,
 // all terms read from the row before the pass), so the dependent chain of
-// barriers is n/K long.
+// barriers is n/K long (K = 2: each pass costs about as many remote loads as
+// cells x 2^K, so 2 items per pass measured fastest, 1 and 3 close behind).
 #include <cooperative_groups.h>
 
 #include "llp_common.cuh"
@@ -55,7 +56,10 @@ __global__ void __launch_bounds__(kKnapThreads) knapsack_single(int32_t n, const
 }
 
 constexpr int kClusterThreads = 1024;
-constexpr int kClusterK = 3;        // items per pass
+#ifndef LLP_KNAP_CLUSTER_K
+#define LLP_KNAP_CLUSTER_K 2
+#endif
+constexpr int kClusterK = LLP_KNAP_CLUSTER_K;  // items per pass
 constexpr int kClusterCells = 4;    // cells per thread in flight
 
 // Address of the int32 at shared-memory offset `a` (bytes, this CTA's window) in

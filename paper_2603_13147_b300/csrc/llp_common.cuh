@@ -66,6 +66,7 @@ struct alignas(256) WsHeader {
     uint32_t sched_delta;
     int32_t sched_cfg;
     int32_t sched_chain;
+    int32_t sched_gw;       // dense-sweep group width, 0 = the grid-size rule
     int32_t sched_valid;
     float feat[16];  // instance features the choice was made from
     float feat_wmax; // largest sampled arc weight

@@ -1,8 +1,9 @@
 // Learned scheduler of the graph sweep (an adaptive choice of solver, which the
 // paper leaves to future work in its conclusion): a small MLP
-//     16 instance features -> 64 -> 64 -> logits of four softmax heads
+//     16 instance features -> 64 -> 64 -> logits of five softmax heads
 //     {sweep mode (3), bucket-width class (8), work-block configuration (3),
-//      local-chain class (4: off, 4, 16, 64 batches)}
+//      local-chain class (4: off, 4, 16, 64 batches),
+//      dense-sweep group-width class (5: the grid-size rule, 1, 2, 4, 8 words)}
 // with ReLU activations, fp32.  It only picks the schedule of a run; the
 // schedule never changes the result (every schedule reaches the same least
 // fixed point), so a bad choice only costs time.
@@ -222,6 +223,11 @@ __global__ void mlp_schedule_kernel(const float *params, MlpDims d, WsHeader *h)
             const int ch = argmax_head(z, d.heads[0] + d.heads[1] + d.heads[2], d.heads[3]);
             h->sched_chain = ch == 0 ? 0 : (1 << (2 * ch));  // 0, 4, 16, 64
         }
+        h->sched_gw = 0;
+        if (d.nheads > 4) {
+            const int gc = argmax_head(z, d.heads[0] + d.heads[1] + d.heads[2] + d.heads[3], d.heads[4]);
+            h->sched_gw = gc == 0 ? 0 : (1 << (gc - 1));  // rule, 1, 2, 4, 8
+        }
         h->sched_valid = 1;
     }
 }
@@ -389,12 +395,13 @@ llp_status_t enqueue_learned_schedule(const llp_csr_t *g, int32_t source, bool u
     d.F = 16;
     d.H1 = 64;
     d.H2 = 64;
-    d.O = 18;
-    d.nheads = 4;
+    d.O = 23;
+    d.nheads = 5;
     d.heads[0] = 3;
     d.heads[1] = 8;
     d.heads[2] = 3;
     d.heads[3] = 4;
+    d.heads[4] = 5;
     const uint32_t *w = unit ? nullptr : g->weights;
     if (g->offsets_64)
         graph_features_kernel<int64_t><<<kFeatBlocks, kFeatThreads, 0, st>>>(g->n, g->m, (const int64_t *)g->offsets,
@@ -487,6 +494,7 @@ llp_status_t llp_graph_schedule(const llp_csr_t *g, int32_t source, int32_t unit
             h_chosen->delta = hh.sched_delta;
             h_chosen->block_cfg = hh.sched_cfg;
             h_chosen->local_chain = hh.sched_chain;
+            h_chosen->group_words = hh.sched_gw;
         }
         if (h_features)
             for (int i = 0; i < 16; i++) h_features[i] = hh.feat[i];

@@ -1,10 +1,12 @@
 """Learned scheduler of the graph sweep: training data, training, model file.
 
-The network (features -> 64 -> 64 -> {mode, bucket-width class, block_cfg})
+The network (features -> 64 -> 64 -> {mode, bucket-width class, block_cfg,
+local-chain class, dense-sweep group-width class})
 runs on the device inside llp_sssp / llp_bfs when llp_sched_t.use_mlp = 1.
 Training data are timings of the plain engine: for each generated graph, the
-schedule space is searched coordinate-wise (bucket width, then mode, then
-block configuration; each candidate timed with CUDA events, median of 3), and
+schedule space is searched coordinate-wise (bucket width, mode, local chain,
+block configuration, group width; each candidate timed with CUDA events, median
+of 3), and
 the fastest schedule becomes the label.  The features come from the same device
 feature kernel the engine uses at run time.  Training is full-batch Adam with
 the library's own fp32 forward/backward/Adam kernels.  The schedule never
@@ -62,12 +64,14 @@ def _time_call(fn, reps=3, cap_ms=None):
 
 
 CHAIN_OF_CLASS = (0, 4, 16, 64)
+GW_OF_CLASS = (0, 1, 2, 4, 8)  # 0: the engine's grid-size rule
 
 
 def label_graph(dg: B.DeviceGraph, source: int, unit: bool, wmax: int, ws=None, passes: int = 2,
                 margin: float = 0.03):
-    """Coordinate search over (mode, bucket class, block class, chain class), starting from the
-    heuristic default; a coordinate moves only when a candidate is faster by more than `margin`.
+    """Coordinate search over (mode, bucket class, block class, chain class, group-width class),
+    starting from the heuristic default; a coordinate moves only when a candidate is faster by more
+    than `margin`.
     Returns (label tuple of class indices, timing log, best ms)."""
     if ws is None:
         ws = B.workspace(B.sssp_workspace_size(dg.n, dg.m), dg.indices.device)
@@ -80,14 +84,15 @@ def label_graph(dg: B.DeviceGraph, source: int, unit: bool, wmax: int, ws=None, 
         if key in log:
             return log[key]
         s = B.make_sched(mode=lab[0], delta=delta_of_class(lab[1], wmax), block_cfg=lab[2] + 1,
-                         local_chain=CHAIN_OF_CLASS[lab[3]] if lab[3] else -1)
+                         local_chain=CHAIN_OF_CLASS[lab[3]] if lab[3] else -1, group_words=GW_OF_CLASS[lab[4]])
         t = _time_call(lambda: fn(dg, source, out=out, sched=s, ws=ws), cap_ms=cap)
         log[key] = t
         return t
 
-    best = [0, 0, 1, 0]  # AUTO, no buckets, block cfg 2, no chain: the heuristic default
+    best = [0, 0, 1, 0, 0]  # AUTO, no buckets, block cfg 2, no chain, group-width rule: the heuristic
     best_t = run(best, None)
-    axes = [(1, [0] if unit else list(range(N_DELTA_CLASSES))), (0, [0, 1, 2]), (3, [0, 1, 2, 3]), (2, [0, 1, 2])]
+    axes = [(1, [0] if unit else list(range(N_DELTA_CLASSES))), (0, [0, 1, 2]), (3, [0, 1, 2, 3]), (2, [0, 1, 2]),
+            (4, [0, 1, 2, 3, 4])]
     for _ in range(passes):
         moved = False
         for ax, vals in axes:
@@ -105,9 +110,11 @@ def label_graph(dg: B.DeviceGraph, source: int, unit: bool, wmax: int, ws=None, 
 
 
 def label_to_sched(label, wmax: int) -> B.Sched:
-    """Class tuple (mode, bucket class, block class 0..2, chain class 0..3) -> schedule."""
+    """Class tuple (mode, bucket class, block class 0..2, chain class 0..3, group-width class 0..4) ->
+    schedule."""
     return B.make_sched(mode=int(label[0]), delta=delta_of_class(int(label[1]), wmax), block_cfg=int(label[2]) + 1,
-                        local_chain=CHAIN_OF_CLASS[int(label[3])] if int(label[3]) else -1)
+                        local_chain=CHAIN_OF_CLASS[int(label[3])] if int(label[3]) else -1,
+                        group_words=GW_OF_CLASS[int(label[4])])
 
 
 def training_graphs(seed: int = 11, quick: bool = False):
@@ -123,7 +130,12 @@ def training_graphs(seed: int = 11, quick: bool = False):
         g = synth.rmat_graph(sc, 16, 0.45, 0.22, 0.22, 1, 255, seed=int(rng.integers(1 << 30)))
         items.append((f"rmat{sc}_flat", g, synth.max_out_degree_vertex(g), False))
         items.append((f"rmat{sc}_bfs", g, synth.max_out_degree_vertex(g), True))
-    sides = [64, 128, 256] if quick else [64, 128, 256, 384, 512, 768, 1024]
+    if not quick:
+        # larger power-law instances (block configuration and group width matter more there)
+        for sc in (21, 22):
+            g = synth.rmat_graph(sc, 16, 0.57, 0.19, 0.19, 1, 255, seed=int(rng.integers(1 << 30)))
+            items.append((f"rmat{sc}_ef16_w255", g, synth.max_out_degree_vertex(g), False))
+    sides = [64, 128, 256] if quick else [64, 128, 256, 384, 512, 768, 1024, 1280]
     for side in sides:
         for whi in (1000, 100):
             g = synth.grid_graph(side, side, 1, whi, seed=int(rng.integers(1 << 30)))
@@ -204,7 +216,12 @@ def save_model(params: torch.Tensor, path: str = MODEL_PATH, meta=None):
 
 
 def load_model(path: str = MODEL_PATH, device="cuda") -> torch.Tensor:
+    """The trained parameters; refuses a file whose size does not match the network's shape
+    (the device kernels read exactly that many parameters)."""
     z = np.load(path)
+    want = B.mlp_param_count(B.mlp_dims())
+    if z["params"].size != want:
+        raise ValueError(f"scheduler model {path} has {z['params'].size} parameters, the network needs {want}")
     return torch.from_numpy(z["params"].astype(np.float32)).to(device)
 
 

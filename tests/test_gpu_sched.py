@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 F, H1, H2 = 16, 64, 64
-HEADS = [3, 8, 3, 4]
+HEADS = [3, 8, 3, 4, 5]
 O = sum(HEADS)
 
 
@@ -80,7 +80,7 @@ def test_training_reduces_loss(llp):
     rng = np.random.default_rng(5)
     X = rng.normal(0, 1, (64, F)).astype(np.float32)
     Y = np.stack([(X[:, 0] > 0).astype(int), (X[:, 1] > 0).astype(int) * 3, (X[:, 2] > 0).astype(int),
-                  (X[:, 3] > 0).astype(int) * 2], 1)
+                  (X[:, 3] > 0).astype(int) * 2, (X[:, 4] > 0).astype(int) * 4], 1)
     params, hist = sched.train(X, Y.astype(np.int32), steps=400, lr=1e-2)
     assert hist[-1][1] < 0.5 * hist[0][1]
     assert (sched.predict(params, X) == Y).mean() > 0.9
@@ -99,10 +99,11 @@ def test_device_inference_matches_oracle_network(llp):
         z, _ = omlp.forward(th.astype(np.float64), np.array([feats], np.float64), F, H1, H2, O)
         z = z[0]
         pred = [int(np.argmax(z[0:3])), int(np.argmax(z[3:11])), int(np.argmax(z[11:14])),
-                int(np.argmax(z[14:18]))]
+                int(np.argmax(z[14:18])), int(np.argmax(z[18:23]))]
         assert chosen.mode == pred[0]
         assert chosen.block_cfg == pred[2] + 1
         assert chosen.local_chain == sched.CHAIN_OF_CLASS[pred[3]]
+        assert chosen.group_words == sched.GW_OF_CLASS[pred[4]]
         want = sched.delta_of_class(pred[1], sched.sampled_wmax(g))
         assert chosen.delta == want
 
