@@ -43,13 +43,16 @@
 // neither reads nor writes it.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "llp_common.cuh"
+#include "sweep_init.cuh"
 
 namespace llp {
 
-llp_status_t enqueue_learned_schedule(const llp_csr_t *g, int32_t source, bool unit, const float *params,
-                                      WsHeader *h, cudaStream_t st);
+template <typename OffT>
+llp_status_t enqueue_learned_prologue(const llp_csr_t *g, int32_t source, bool unit, const float *params, WsHeader *h,
+                                      const SweepInit<OffT> &init, cudaStream_t st);
 size_t lb_workspace_bytes(int32_t n, int64_t m);
 llp_status_t lb_launch(bool unit, const llp_csr_t *g, int32_t source, uint32_t *dist, uint32_t *bm0, uint32_t *bm1,
                        void *lists, WsHeader *h, long long deadline_ns, int32_t mode, unsigned long long dense_arcs,
@@ -111,6 +114,7 @@ struct GraphArgs {
     int32_t chunk_edges;
     int32_t cfg;
     int32_t use_dev_sched;  // 1: take mode/delta/cfg from the header (learned scheduler)
+    int32_t pre_init;       // 1: the state was initialised by the learned scheduler's prologue
     int32_t local_chain;    // batches per worklist item of the local chain, 0 = off
     int32_t group_words;    // dense sweeps: bitmap words per item (1, 2, 4, 8), 0 = from the grid size
     long long deadline_ns;
@@ -840,29 +844,18 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
     }
 
     // ---- init_global_state / initial_states_to_process (paper Sec. 3.3)
-    // eight groups of 32 vertices per warp and iteration (loads in flight together);
-    // a warm start keeps the caller's dist[] as the initial state
-    for (int64_t base = gwarp * 256; base < a.n; base += nwarps * 256) {
-        uint32_t deg[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int64_t v = base + 32 * q + lane_id();
-            deg[q] = v < a.n ? (uint32_t)(__ldg(a.off + v + 1) - __ldg(a.off + v)) : 0u;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int64_t v = base + 32 * q + lane_id();
-            if (v < a.n && (!a.warm || v == a.source)) a.dist[v] = (v == a.source) ? 0u : kInf;
-            const uint32_t has = __ballot_sync(0xffffffffu, deg[q] > 0);
-            const uint32_t large = __ballot_sync(0xffffffffu, deg[q] > (uint32_t)c.small_max);
-            if (lane_id() == 0 && base + 32 * q < a.n) {
-                const int64_t wi = (base >> 5) + q;
-                a.cls[wi] = make_uint2(has, large);
-                if (a.fixed) a.fixed[wi] = 0u;
-                a.bm[0][wi] = 0u;
-                a.bm[1][wi] = 0u;
-                a.bm[2][wi] = 0u;
-            }
+    // a learned run had the state initialised by its prologue (for the default block
+    // configuration); only the large bits change when the chosen one differs
+    if (!a.pre_init) {
+        const SweepInit<OffT> ini{a.n, a.source, a.warm, (uint32_t)c.small_max, a.off, a.dist, a.cls,
+                                  a.bm[0], a.bm[1], a.bm[2], a.fixed};
+        sweep_init(ini, gwarp, nwarps);
+    } else if (c.small_max != a.small_max) {
+        for (int64_t base = gwarp * 32; base < a.n; base += nwarps * 32) {
+            const int64_t v = base + lane_id();
+            const uint32_t deg = v < a.n ? (uint32_t)(__ldg(a.off + v + 1) - __ldg(a.off + v)) : 0u;
+            const uint32_t large = __ballot_sync(0xffffffffu, deg > (uint32_t)c.small_max);
+            if (lane_id() == 0) a.cls[base >> 5].y = large;
         }
     }
     if (gtid == 0) {
@@ -1206,10 +1199,6 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
     const int ppm = s ? s->pull_permille : 0;
     const bool pull_on = UNIT && gin && ppm >= 0;
     const unsigned long long pull_arcs = (unsigned long long)g->m * (unsigned long long)(ppm > 0 ? ppm : 200) / 1000ull;
-    if (learned) {
-        rc = enqueue_learned_schedule(g, source, UNIT, s->mlp_params, (WsHeader *)ws, stream);
-        if (rc != LLP_OK) return rc;
-    }
 
     // Block configuration 4 selects the load-balanced engine (lb_sweep.cu): one worklist (no
     // buckets), no local chain, no pull sweeps, the schedule chosen on the host, int32 offsets.
@@ -1255,6 +1244,7 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         args.chunk_edges = bc.chunk;
         args.cfg = cfg;
         args.use_dev_sched = learned ? 1 : 0;
+        args.pre_init = learned ? 1 : 0;
         args.local_chain = (s && s->local_chain > 0) ? s->local_chain : 0;
         args.group_words = s ? s->group_words : 0;
         args.deadline_ns = deadline_from(s);
@@ -1262,10 +1252,22 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         args.n_seeds = n_seeds > 0 ? n_seeds : 0;
         args.seeds = seeds;
     };
+    // a learned run: one prologue launch computes the schedule (features + network) while its
+    // other CTAs initialise the state for the default block configuration
+    auto prologue = [&](const auto &args) -> llp_status_t {
+        using OffT = std::remove_cv_t<std::remove_pointer_t<decltype(args.off)>>;
+        const SweepInit<OffT> ini{args.n, args.source, args.warm, (uint32_t)args.small_max, args.off, args.dist,
+                                  args.cls, args.bm[0], args.bm[1], args.bm[2], args.fixed};
+        return enqueue_learned_prologue<OffT>(g, source, UNIT, s->mlp_params, (WsHeader *)ws, ini, stream);
+    };
     if (g->offsets_64) {
         GraphArgs<int64_t> args;
         fill(args);
         args.off = (const int64_t *)g->offsets;
+        if (learned) {
+            rc = prologue(args);
+            if (rc != LLP_OK) return rc;
+        }
         args.in_off = pull_on ? (const int64_t *)gin->offsets : nullptr;
         void *kargs[] = {&args};
         const void *fn = (const void *)graph_sweep_kernel<int64_t, UNIT, false>;
@@ -1277,6 +1279,10 @@ llp_status_t graph_solve(const llp_csr_t *g, int32_t source, uint32_t *out, cons
         GraphArgs<int32_t> args;
         fill(args);
         args.off = (const int32_t *)g->offsets;
+        if (learned) {
+            rc = prologue(args);
+            if (rc != LLP_OK) return rc;
+        }
         args.in_off = pull_on ? (const int32_t *)gin->offsets : nullptr;
         void *kargs[] = {&args};
         const void *fn = (const void *)graph_sweep_kernel<int32_t, UNIT, false>;

@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "llp_common.cuh"
+#include "sweep_init.cuh"
 
 namespace llp {
 
@@ -42,11 +43,13 @@ constexpr int kFeatThreads = 256;
 constexpr int kFeatSamples = 16384;  // vertices and arcs sampled (evenly spaced)
 
 // Instance features from an evenly spaced sample of vertices (degree
-// histogram, mean and max degree) and arcs (weight range and spread).  Many
-// CTAs accumulate into the header; the last CTA to finish writes the features.
+// histogram, mean and max degree) and arcs (weight range and spread).  CTAs
+// cta = 0 .. ncta-1 accumulate into the header; the last CTA to finish writes
+// the features and returns true (to all its threads).  Every thread of a
+// participating CTA calls it.
 template <typename OffT>
-__global__ void __launch_bounds__(kFeatThreads) graph_features_kernel(int32_t n, int64_t m, const OffT *off,
-                                                                      const uint32_t *w, int32_t source, WsHeader *h) {
+__device__ bool features_part(int32_t n, int64_t m, const OffT *off, const uint32_t *w, int32_t source, WsHeader *h,
+                              int cta, int ncta) {
     __shared__ unsigned int s_hist[6];
     __shared__ unsigned long long s_deg;
     __shared__ unsigned int s_maxdeg, s_wmin, s_wmax;
@@ -64,10 +67,10 @@ __global__ void __launch_bounds__(kFeatThreads) graph_features_kernel(int32_t n,
     __syncthreads();
     const int32_t S = n < kFeatSamples ? n : kFeatSamples;
     const int64_t Sw = m < kFeatSamples ? m : kFeatSamples;
-    const int stride = gridDim.x * blockDim.x;
+    const int stride = ncta * blockDim.x;
     unsigned long long dsum = 0;
     unsigned int dmax = 0;
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < S; i += stride) {
+    for (int32_t i = cta * blockDim.x + threadIdx.x; i < S; i += stride) {
         const int64_t v = (int64_t)i * n / S;
         const unsigned int d = (unsigned int)(off[v + 1] - off[v]);
         const int b = d == 0 ? 0 : d < 4 ? 1 : d < 16 ? 2 : d < 64 ? 3 : d < 256 ? 4 : 5;
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(kFeatThreads) graph_features_kernel(int32_t n,
     }
     unsigned int wmn = 0xFFFFFFFFu, wmx = 0;
     float ws = 0.f, wq = 0.f;
-    for (int64_t i = blockIdx.x * blockDim.x + threadIdx.x; i < Sw && w; i += stride) {
+    for (int64_t i = (int64_t)cta * blockDim.x + threadIdx.x; i < Sw && w; i += stride) {
         const unsigned int x = w[i * m / Sw];
         wmn = min(wmn, x);
         wmx = max(wmx, x);
@@ -113,10 +116,11 @@ __global__ void __launch_bounds__(kFeatThreads) graph_features_kernel(int32_t n,
         atomicAdd(&h->feat[3], s_wsum);
         atomicAdd(&h->feat[4], s_wsq);
         __threadfence();
-        s_last = atomicAdd(&h->scratch[15], 1u) + 1u == gridDim.x;
+        s_last = atomicAdd(&h->scratch[15], 1u) + 1u == (unsigned)ncta;
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last) return false;
+    if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int maxdeg = *(volatile unsigned int *)&h->feat[0];
     const unsigned int swmax = *(volatile unsigned int *)&h->feat[1];
@@ -144,6 +148,16 @@ __global__ void __launch_bounds__(kFeatThreads) graph_features_kernel(int32_t n,
     f[14] = log2f((float)sdeg + 1.f) - f[2];
     f[15] = 1.f;
     h->feat_wmax = wmax;
+    __threadfence();
+    }
+    __syncthreads();
+    return true;
+}
+
+template <typename OffT>
+__global__ void __launch_bounds__(kFeatThreads) graph_features_kernel(int32_t n, int64_t m, const OffT *off,
+                                                                      const uint32_t *w, int32_t source, WsHeader *h) {
+    features_part(n, m, off, w, source, h, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------- inference
@@ -156,14 +170,14 @@ __device__ __forceinline__ int argmax_head(const float *z, int lo, int len) {
 }
 
 // One CTA (>= max(H1, H2, O) threads): MLP on h->feat, then the schedule.
-// The parameters are first copied to shared memory with independent loads
-// (the layer loops then read shared memory instead of waiting on one global
-// load per step); networks larger than the buffer read them in place.
+// The parameters are first copied to shared memory (sp, kSchedSmemParams
+// floats) with independent loads (the layer loops then read shared memory
+// instead of waiting on one global load per step); networks larger than the
+// buffer read them in place.  Every thread of the CTA calls it.
 constexpr int kSchedSmemParams = 8192;
 constexpr int kSchedThreads = 256;  // >= kMaxDim; all threads copy the parameters
-__global__ void mlp_schedule_kernel(const float *params, MlpDims d, WsHeader *h) {
-    __shared__ float x[kMaxDim], h1[kMaxDim], h2[kMaxDim], z[kMaxDim];
-    __shared__ float sp[kSchedSmemParams];
+// Copies the parameters into sp when they fit; returns the pointer the network reads.
+__device__ const float *stage_params(const float *params, const MlpDims &d, float *sp) {
     const int t = threadIdx.x;
     const int np = (int)mlp_param_count(d);
     const float *P = params;
@@ -184,6 +198,13 @@ __global__ void mlp_schedule_kernel(const float *params, MlpDims d, WsHeader *h)
         }
         P = sp;
     }
+    return P;
+}
+
+// The network on h->feat with parameters P (shared or global memory), then the schedule.
+__device__ void mlp_infer_header(const float *P, const MlpDims &d, WsHeader *h) {
+    __shared__ float x[kMaxDim], h1[kMaxDim], h2[kMaxDim], z[kMaxDim];
+    const int t = threadIdx.x;
     const float *W1 = P, *b1 = W1 + d.F * d.H1, *W2 = b1 + d.H1, *b2 = W2 + d.H1 * d.H2, *W3 = b2 + d.H2,
                 *b3 = W3 + d.H2 * d.O;
     if (t < d.F) x[t] = h->feat[t];
@@ -229,6 +250,33 @@ __global__ void mlp_schedule_kernel(const float *params, MlpDims d, WsHeader *h)
             h->sched_gw = gc == 0 ? 0 : (1 << (gc - 1));  // rule, 1, 2, 4, 8
         }
         h->sched_valid = 1;
+    }
+}
+
+__global__ void mlp_schedule_kernel(const float *params, MlpDims d, WsHeader *h) {
+    __shared__ float sp[kSchedSmemParams];
+    const float *P = stage_params(params, d, sp);
+    mlp_infer_header(P, d, h);
+}
+
+// The learned scheduler's prologue of a graph sweep: CTAs 0 .. kFeatBlocks-1
+// sample the instance, the last of them runs the network; every other CTA
+// initialises the sweep's state meanwhile (so a learned run pays for the
+// schedule inside the time the initialisation takes anyway).
+template <typename OffT>
+__global__ void __launch_bounds__(kFeatThreads) learned_prologue_kernel(int32_t n, int64_t m, const OffT *off,
+                                                                        const uint32_t *w, int32_t source,
+                                                                        WsHeader *h, const float *params, MlpDims d,
+                                                                        SweepInit<OffT> init) {
+    __shared__ float sp[kSchedSmemParams];
+    if (blockIdx.x < kFeatBlocks) {
+        // the parameters are staged while sampling (whichever CTA finishes last runs the network)
+        const float *P = stage_params(params, d, sp);
+        if (features_part(n, m, off, w, source, h, blockIdx.x, kFeatBlocks)) mlp_infer_header(P, d, h);
+    } else {
+        const int wpb = blockDim.x >> 5;
+        sweep_init(init, (int64_t)(blockIdx.x - kFeatBlocks) * wpb + (threadIdx.x >> 5),
+                   (int64_t)(gridDim.x - kFeatBlocks) * wpb);
     }
 }
 
@@ -413,6 +461,33 @@ llp_status_t enqueue_learned_schedule(const llp_csr_t *g, int32_t source, bool u
     LLP_CUDA_TRY(cudaGetLastError());
     return LLP_OK;
 }
+
+// The prologue launch of a learned graph sweep (features + network + state initialisation).
+template <typename OffT>
+llp_status_t enqueue_learned_prologue(const llp_csr_t *g, int32_t source, bool unit, const float *params, WsHeader *h,
+                                      const SweepInit<OffT> &init, cudaStream_t st) {
+    MlpDims d{};
+    d.F = 16;
+    d.H1 = 64;
+    d.H2 = 64;
+    d.O = 23;
+    d.nheads = 5;
+    d.heads[0] = 3;
+    d.heads[1] = 8;
+    d.heads[2] = 3;
+    d.heads[3] = 4;
+    d.heads[4] = 5;
+    const DeviceInfo di = device_info();
+    const int init_ctas = std::max(1, (di.sms > 0 ? di.sms : 148) * 6 - kFeatBlocks);
+    learned_prologue_kernel<OffT><<<kFeatBlocks + init_ctas, kFeatThreads, 0, st>>>(
+        g->n, g->m, (const OffT *)g->offsets, unit ? nullptr : g->weights, source, h, params, d, init);
+    LLP_CUDA_TRY(cudaGetLastError());
+    return LLP_OK;
+}
+template llp_status_t enqueue_learned_prologue<int32_t>(const llp_csr_t *, int32_t, bool, const float *, WsHeader *,
+                                                        const SweepInit<int32_t> &, cudaStream_t);
+template llp_status_t enqueue_learned_prologue<int64_t>(const llp_csr_t *, int32_t, bool, const float *, WsHeader *,
+                                                        const SweepInit<int64_t> &, cudaStream_t);
 
 }  // namespace llp
 

@@ -135,7 +135,7 @@ def training_graphs(seed: int = 11, quick: bool = False):
         for sc in (21, 22, 23, 24):
             g = synth.rmat_graph(sc, 16, 0.57, 0.19, 0.19, 1, 255, seed=int(rng.integers(1 << 30)))
             items.append((f"rmat{sc}_ef16_w255", g, synth.max_out_degree_vertex(g), False))
-    sides = [64, 128, 256] if quick else [64, 128, 256, 384, 512, 768, 1024, 1280]
+    sides = [64, 128, 256] if quick else [64, 128, 256, 384, 512, 768, 1024, 1280, 1536, 2048]
     for side in sides:
         for whi in (1000, 100):
             g = synth.grid_graph(side, side, 1, whi, seed=int(rng.integers(1 << 30)))

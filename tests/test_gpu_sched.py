@@ -135,3 +135,34 @@ def test_trained_model_loads_and_schedules(llp):
     dg = llp.DeviceGraph.from_host(g, "cuda")
     d, ws = llp.sssp(dg, 0, sched=sched.learned_sched(p))
     assert (llp.as_u32(d) == oracle.sssp(g["offsets"], g["indices"], g["weights"], 0)).all()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_learned_prologue_with_warm_start_pull_and_int64(llp, seed):
+    """The learned run's prologue initialises the state (keeping a warm start's distances), and
+    the sweep rebuilds the class table when the chosen block configuration moves the degree limit:
+    warm starts, BFS with pull sweeps and int64 offsets stay identical to the oracle under random
+    networks."""
+    from paper_2603_13147_b300 import sched
+    th = torch.tensor(sched.init_params(200 + seed) * 3.0, device="cuda")
+    learned = llp.make_sched(use_mlp=1, mlp_params=th)
+    g = synth.rmat(14, seed=20 + seed)
+    s = synth.max_out_degree_vertex(g)
+    ref = oracle.sssp(g["offsets"], g["indices"], g["weights"], s)
+    # warm start: the oracle result of slightly heavier weights, then the true weights
+    w_up = g["weights"].copy()
+    w_up[::7] += 5
+    prev = oracle.sssp(g["offsets"], g["indices"], w_up, s)
+    dg = llp.DeviceGraph.from_host(g, "cuda")
+    dist = torch.from_numpy(prev.view(np.int32).copy()).cuda()
+    seeds = torch.from_numpy(np.unique(np.searchsorted(g["offsets"], np.arange(0, g["m"], 7), side="right") - 1)
+                             .astype(np.int32)).cuda()
+    d, ws = llp.sssp_warm(dg, s, dist, seeds, sched=learned)
+    assert llp.get_status(ws)["status"] == 0
+    assert (llp.as_u32(d) == ref).all()
+    # BFS with pull sweeps over the device transpose
+    lv, ws = llp.bfs_pull(dg, dg.transpose(), s, sched=learned, ws=ws)
+    assert (llp.as_u32(lv) == oracle.bfs(g["offsets"], g["indices"], s)).all()
+    # int64 offsets
+    d64, ws = llp.sssp(llp.DeviceGraph.from_host(g, "cuda", offsets_64=True), s, sched=learned, ws=ws)
+    assert (llp.as_u32(d64) == ref).all()
