@@ -28,7 +28,13 @@
 //     device's random-access rate);
 //   - the advance itself is a fire-and-forget atomic min on dist[v] issued
 //     when the candidate beats the value just read (a stale read only costs a
-//     redundant visit: distances only decrease);
+//     redundant visit: distances only decrease); the advanced targets wait in
+//     a per-warp buffer and enter the next worklist in bulk (class lookup,
+//     bitmap dedup, appends), so a batch of arcs ends at the read of d(v);
+//   - the per-CTA state of the run (schedule, bucket bounds, bitmap pointers,
+//     sweep flags) lives in shared memory, written by one thread per sweep,
+//     and one thread per CTA reads the sweep's worklist sizes: registers stay
+//     free for the arcs in flight;
 //   - with a finite bucket width delta (the paper's bucket worklist, Sec. 3.3)
 //     only advances with d below the current bucket bound enter the next
 //     worklist; the others wait in a far list filtered when the near worklist
@@ -125,38 +131,73 @@ struct GraphArgs {
     const int32_t *seeds;
 };
 
+// Buffer selection by sweep parity / rotation without indexing the parameter
+// arrays with a run-time value (which would copy the arguments to the stack).
+template <typename T>
+__device__ __forceinline__ T *pick2(T *const (&arr)[2], uint32_t i) { return (i & 1u) ? arr[1] : arr[0]; }
+template <typename T>
+__device__ __forceinline__ T *pick3(T *const (&arr)[3], uint32_t i) {
+    const uint32_t r = i % 3u;
+    return r == 0 ? arr[0] : (r == 1 ? arr[1] : arr[2]);
+}
+
+// Per-thread (mostly warp-uniform) state of a run.
 struct SweepCtx {
-    // schedule of this run (from the arguments, or chosen on the device)
-    int32_t mode, cfg, small_max, chunk_edges;
-    int32_t gw;                    // dense sweeps: bitmap words per item
-    uint32_t delta;
     uint32_t k;                    // current sweep
+    uint32_t lq_n = 0;             // entries on the warp's local-chain stack
+    bool chain_on = false;         // the local chain is active in this warp
+    uint32_t items = 0, adv = 0;   // statistics of the run
+    uint32_t edges = 0;            // arcs examined in this sweep (lane 0 mostly)
+    uint32_t marked = 0;           // dense_next marks (an upper bound of the next frontier)
+    uint32_t st_ns = 0, st_nc = 0; // staged worklist appends of the warp (warp-uniform)
+    uint32_t pend_n = 0;           // deferred advances in g_pend (warp-uniform)
+};
+
+// Per-CTA state of a run that every thread reads: written by thread 0 at the
+// start of the run and of each sweep, read after a CTA barrier.  Keeping it in
+// shared memory keeps the sweep's registers for the arcs in flight.
+struct SweepShared {
     unsigned long long bucket_hi;  // exclusive bound of the current bucket
     unsigned long long fixed_lo;   // every d below it is final (the previous bucket's bound)
+    unsigned long long next_hi;    // bound of the next bucket (taken at the start of the next sweep)
+    uint32_t *bm_cur, *bm_next;    // B_k and B_{k+1}
+    int32_t mode, cfg, small_max, chunk_edges;
+    int32_t gw;                    // dense sweeps: bitmap words per item
+    int32_t chain;                 // batches of 32 a warp may take from its stack per worklist item
+    uint32_t delta;
     uint32_t fa;                   // far-list generation
+    uint32_t ns, nc, nf, fmin;     // sizes of the sweep's worklists, far list and its least candidate
+    bool dense;                    // this sweep scans B_k
     bool dense_next;               // small advances only set their bitmap bit
-    bool pull = false;             // this sweep runs over the in-arcs
-    bool vis_valid = false;        // a.vis holds every vertex reached so far
-    // local chaining (recency-biased per-warp bag): advanced small vertices are
-    // expanded by the same warp within the sweep, LIFO, from a shared-memory stack
-    int32_t *lq;
-    uint32_t lq_n = 0;
-    int32_t chain = 0;             // batches of 32 a warp may take from its stack per worklist item
-    bool chain_on = false;
-    uint32_t *bm_cur, *bm_next;
-    unsigned long long items = 0, edges = 0, adv = 0;
-    uint32_t marked = 0;           // dense_next marks (an upper bound of the next frontier)
-    unsigned long long edges_flushed = 0;
-    // per-warp shared-memory staging of worklist appends (warp-uniform counts)
-    int32_t *st_small;
-    int2 *st_chunk;
-    uint32_t st_ns = 0, st_nc = 0;
+    bool pull;                     // this sweep runs over the in-arcs
+    bool prev_pull;                // the previous sweep ran over the in-arcs
+    bool vis_valid;                // a.vis holds every vertex reached so far
+    bool advance_bucket;           // the next sweep starts the bucket next_hi
 };
+
 
 constexpr uint32_t kStageSmall = 128;  // entries per warp
 constexpr uint32_t kStageChunk = 128;
 constexpr uint32_t kDirectChunks = 4;  // a lane with more chunk entries reserves them directly
 constexpr uint32_t kLocalQ = 128;      // per-warp stack of the local chain
+
+__shared__ SweepShared g_sh;
+__shared__ int32_t g_stage_small[16][kStageSmall];  // per warp
+__shared__ int2 g_stage_chunk[16][kStageChunk];
+__shared__ int32_t g_lq[16][kLocalQ];
+// Deferred worklist insertion: a relaxation that advances v only issues the atomic
+// min and records v in its warp's buffer; the class lookup and the bitmap/list
+// insertion of the buffered targets run in bulk once kPendT of them are pending
+// (and at the end of the sweep), so a batch's chain of dependent loads ends at
+// the read of d(v).  The "advanced again" bits of the next frontier are set later
+// than the advance itself, which lets a few more stale vertices be expanded.
+#ifndef LLP_DEFER
+#define LLP_DEFER 64
+#endif
+constexpr uint32_t kPendT = LLP_DEFER;
+constexpr uint32_t kPendCap = kPendT + 32 * kUnroll;  // at most kPendT - 1 + one batch
+__shared__ int32_t g_pend[16][kPendCap];
+__device__ __forceinline__ int warp_in_cta() { return threadIdx.x >> 5; }
 
 // Moves a warp's staged entries to the global list (one reservation).
 template <typename T>
@@ -203,7 +244,7 @@ __device__ __forceinline__ void append_new(const GraphArgs<OffT> &a, const bool 
         n_small += (newly[j] && cls[j] == 1);
         if (newly[j] && cls[j] == 2) {
             const uint32_t deg = (uint32_t)(__ldg(a.off + v[j] + 1) - __ldg(a.off + v[j]));
-            nch[j] = (deg + c.chunk_edges - 1) / c.chunk_edges;
+            nch[j] = (deg + g_sh.chunk_edges - 1) / g_sh.chunk_edges;
             n_large += nch[j];
         }
     }
@@ -217,11 +258,11 @@ __device__ __forceinline__ void append_new(const GraphArgs<OffT> &a, const bool 
             if (lane_id() >= o) incl += t;
         }
         const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-        if (c.st_ns + tot > kStageSmall) stage_flush(c.st_small, c.st_ns, a.small[nk & 1], &a.h->n_small[nx]);
+        if (c.st_ns + tot > kStageSmall) stage_flush(g_stage_small[warp_in_cta()], c.st_ns, pick2(a.small, nk), &a.h->n_small[nx]);
         uint32_t slot = c.st_ns + incl - n_small;
 #pragma unroll
         for (int j = 0; j < U; j++)
-            if (newly[j] && cls[j] == 1) c.st_small[slot++] = v[j];
+            if (newly[j] && cls[j] == 1) g_stage_small[warp_in_cta()][slot++] = v[j];
         c.st_ns += tot;
     }
     if (__any_sync(0xffffffffu, n_large > 0)) {
@@ -229,7 +270,7 @@ __device__ __forceinline__ void append_new(const GraphArgs<OffT> &a, const bool 
         const bool direct = n_large > kDirectChunks;
         if (__any_sync(0xffffffffu, direct)) {
             uint32_t slot = warp_reserve(direct ? n_large : 0u, &a.h->n_chunk[nx]);
-            int2 *dst = a.chunk[nk & 1];
+            int2 *dst = pick2(a.chunk, nk);
             if (direct) {
 #pragma unroll
                 for (int j = 0; j < U; j++)
@@ -245,12 +286,12 @@ __device__ __forceinline__ void append_new(const GraphArgs<OffT> &a, const bool 
         }
         const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
         if (tot) {
-            if (c.st_nc + tot > kStageChunk) stage_flush(c.st_chunk, c.st_nc, a.chunk[nk & 1], &a.h->n_chunk[nx]);
+            if (c.st_nc + tot > kStageChunk) stage_flush(g_stage_chunk[warp_in_cta()], c.st_nc, pick2(a.chunk, nk), &a.h->n_chunk[nx]);
             uint32_t slot = c.st_nc + incl - mine;
             if (!direct) {
 #pragma unroll
                 for (int j = 0; j < U; j++)
-                    for (uint32_t q = 0; q < nch[j]; q++) c.st_chunk[slot++] = make_int2(v[j], (int)q);
+                    for (uint32_t q = 0; q < nch[j]; q++) g_stage_chunk[warp_in_cta()][slot++] = make_int2(v[j], (int)q);
             }
             c.st_nc += tot;
         }
@@ -282,7 +323,7 @@ __device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, const bool (
 #pragma unroll
             for (int j = 0; j < U; j++)
                 if (want[j] && cls[j] == 1) {
-                    c.lq[slot++] = v[j];
+                    g_lq[warp_in_cta()][slot++] = v[j];
                     want[j] = false;
                 }
             c.lq_n += tot;
@@ -294,8 +335,8 @@ __device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, const bool (
         newly[j] = false;
         if (want[j] && cls[j] != 0) {
             const uint32_t bit = 1u << (v[j] & 31);
-            uint32_t *word = c.bm_next + (v[j] >> 5);
-            if (c.dense_next && cls[j] == 1) {
+            uint32_t *word = g_sh.bm_next + (v[j] >> 5);
+            if (g_sh.dense_next && cls[j] == 1) {
                 red_or(word, bit);
                 c.marked++;
             } else {
@@ -304,6 +345,30 @@ __device__ __forceinline__ void push_near(const GraphArgs<OffT> &a, const bool (
         }
     }
     append_new(a, newly, v, cls, c);
+}
+
+// Drains the deferred advances of the warp: the targets collected in g_pend get
+// their class and enter the next worklist, kUnroll per lane at a time.
+// Warp-collective.
+template <typename OffT>
+__device__ __forceinline__ void drain_pending(const GraphArgs<OffT> &a, SweepCtx &c) {
+    __syncwarp();
+    for (uint32_t base = 0; base < c.pend_n; base += 32 * kUnroll) {
+        bool want[kUnroll];
+        int32_t v[kUnroll];
+        uint32_t cls[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) {
+            const uint32_t i = base + 32 * j + lane_id();
+            want[j] = i < c.pend_n;
+            v[j] = want[j] ? g_pend[warp_in_cta()][i] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) cls[j] = want[j] ? class_of(a, v[j]) : 0u;
+        push_near(a, want, v, cls, c);
+    }
+    __syncwarp();
+    c.pend_n = 0;
 }
 
 // Evaluate forbidden(v) against candidate distances and advance, for up to
@@ -338,12 +403,12 @@ __device__ __forceinline__ void relax_multi(const GraphArgs<OffT> &a, const bool
             } else if (cand[j] < dv[j]) {
                 red_min32(a.dist + v[j], cand[j]);
                 improved = true;
-            } else if (a.fixed && (unsigned long long)dv[j] < c.fixed_lo) {
+            } else if (a.fixed && (unsigned long long)dv[j] < g_sh.fixed_lo) {
                 red_or(a.fixed + (v[j] >> 5), 1u << (v[j] & 31));  // below every pending bucket: final
             }
         }
         c.adv += improved;
-        near[j] = improved && (unsigned long long)cand[j] < c.bucket_hi;
+        near[j] = improved && (unsigned long long)cand[j] < g_sh.bucket_hi;
         far[j] = improved && !near[j];
         any_far |= far[j];
     }
@@ -354,19 +419,34 @@ __device__ __forceinline__ void relax_multi(const GraphArgs<OffT> &a, const bool
             cnt += far[j];
             if (far[j]) fmin = min(fmin, cand[j]);
         }
-        uint32_t slot = warp_reserve(cnt, &a.h->n_far[c.fa % 3]);
+        uint32_t slot = warp_reserve(cnt, &a.h->n_far[g_sh.fa % 3]);
 #pragma unroll
         for (int j = 0; j < kUnroll; j++) {
             if (!far[j]) continue;
             if (slot < a.far_cap) {
-                a.far[c.fa & 1][slot] = make_int2(v[j], (int)cand[j]);
+                pick2(a.far, g_sh.fa)[slot] = make_int2(v[j], (int)cand[j]);
             } else {
                 near[j] = true;  // far list full: keep it in the near worklist (still correct)
             }
             slot++;
         }
-        if (cnt) atomicMin(&a.h->far_min[c.fa % 3], fmin);
+        if (cnt) atomicMin(&a.h->far_min[g_sh.fa % 3], fmin);
     }
+#if LLP_DEFER
+    if (!c.chain_on) {  // with the local chain the advances go to its stack at once
+        const uint32_t lt = lanemask_lt();
+        uint32_t n = c.pend_n;
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) {
+            const uint32_t m = __ballot_sync(0xffffffffu, near[j]);
+            if (near[j]) g_pend[warp_in_cta()][n + __popc(m & lt)] = v[j];
+            n += __popc(m);
+        }
+        c.pend_n = n;
+        if (n >= kPendT) drain_pending(a, c);
+        return;
+    }
+#endif
 #pragma unroll
     for (int j = 0; j < kUnroll; j++) any_near |= near[j];
     if (__any_sync(0xffffffffu, any_near)) {
@@ -437,16 +517,16 @@ __device__ __forceinline__ void expand_group(const GraphArgs<OffT> &a, bool vali
 }
 
 // Local chain: the warp pops up to 32 vertices at a time from the top of its
-// stack (most recent first) and expands them, for at most c.chain batches;
+// stack (most recent first) and expands them, for at most g_sh.chain batches;
 // whatever is left goes to the next sweep's worklist.  Warp-collective.
 template <typename OffT, bool UNIT>
 __device__ __forceinline__ void drain_local(const GraphArgs<OffT> &a, SweepCtx &c) {
-    int32_t budget = c.chain;
+    int32_t budget = g_sh.chain;
     while (c.lq_n > 0 && budget > 0) {
         __syncwarp();
         const uint32_t cnt = c.lq_n < 32u ? c.lq_n : 32u;
         const bool ok = lane_id() < cnt;
-        const int32_t u = ok ? c.lq[c.lq_n - cnt + lane_id()] : 0;
+        const int32_t u = ok ? g_lq[warp_in_cta()][c.lq_n - cnt + lane_id()] : 0;
         __syncwarp();
         c.lq_n -= cnt;
         budget--;
@@ -458,7 +538,7 @@ __device__ __forceinline__ void drain_local(const GraphArgs<OffT> &a, SweepCtx &
             __syncwarp();
             const uint32_t cnt = c.lq_n < 32u ? c.lq_n : 32u;
             const bool w1[1] = {lane_id() < cnt};
-            const int32_t u1[1] = {w1[0] ? c.lq[c.lq_n - cnt + lane_id()] : 0};
+            const int32_t u1[1] = {w1[0] ? g_lq[warp_in_cta()][c.lq_n - cnt + lane_id()] : 0};
             const uint32_t c1[1] = {w1[0] ? 1u : 0u};
             __syncwarp();
             c.lq_n -= cnt;
@@ -474,10 +554,10 @@ __device__ __forceinline__ void drain_local(const GraphArgs<OffT> &a, SweepCtx &
 template <typename OffT, bool UNIT>
 __device__ __forceinline__ void chunk_body(const GraphArgs<OffT> &a, int32_t y, uint32_t du, OffT b0, OffT e0,
                                            SweepCtx &c) {
-    const OffT beg = b0 + (OffT)y * (OffT)c.chunk_edges;
-    const OffT end = min(e0, beg + (OffT)c.chunk_edges);
+    const OffT beg = b0 + (OffT)y * (OffT)g_sh.chunk_edges;
+    const OffT end = min(e0, beg + (OffT)g_sh.chunk_edges);
     c.items += (lane_id() == 0 && y == 0);
-    c.edges += (lane_id() == 0) ? (unsigned long long)(end - beg) : 0ull;
+    c.edges += (lane_id() == 0) ? (uint32_t)(end - beg) : 0u;
     for (OffT base = beg; base < end; base += 32 * kUnroll) {
         bool ok[kUnroll], ovf[kUnroll];
         int32_t v[kUnroll];
@@ -509,11 +589,11 @@ __device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item
     uint32_t nxt = 0, du = 0;
     OffT b0 = 0, e0 = 0;
     if (lane_id() == 0) {
-        nxt = __ldcg(c.bm_next + (u >> 5));
+        nxt = __ldcg(g_sh.bm_next + (u >> 5));
         du = __ldcg(a.dist + u);
         b0 = __ldg(a.off + u);
         e0 = __ldg(a.off + u + 1);
-        if (item.y == 0) red_and(c.bm_cur + (u >> 5), ~bit);
+        if (item.y == 0) red_and(g_sh.bm_cur + (u >> 5), ~bit);
     }
     nxt = __shfl_sync(0xffffffffu, nxt, 0);
     if (nxt & bit) return;  // warp-uniform
@@ -524,21 +604,21 @@ __device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item
     if (c.chain_on) drain_local<OffT, UNIT>(a, c);
 }
 
-// Dense sweep item: c.gw (<= kGroupWords) bitmap words (32 vertices each), loaded with
+// Dense sweep item: g_sh.gw (<= kGroupWords) bitmap words (32 vertices each), loaded with
 // one coalesced access.  The small vertices whose bit is set (and not set again
 // for the next sweep) are compacted across the words, 32 per expansion, so a
 // warp's lanes stay filled when few vertices of a word are active.  The words
 // are cleared.
 template <typename OffT, bool UNIT>
 __device__ __forceinline__ void scan_words(const GraphArgs<OffT> &a, int64_t g, SweepCtx &c) {
-    const int64_t wi = g * c.gw + lane_id();
+    const int64_t wi = g * g_sh.gw + lane_id();
     uint32_t act = 0;
-    if (lane_id() < c.gw && wi < a.nwords) {
-        const uint32_t b = __ldcg(c.bm_cur + wi);
+    if (lane_id() < g_sh.gw && wi < a.nwords) {
+        const uint32_t b = __ldcg(g_sh.bm_cur + wi);
         const uint32_t large = __ldg(&a.cls[wi].y);
-        const uint32_t again = __ldcg(c.bm_next + wi);
+        const uint32_t again = __ldcg(g_sh.bm_next + wi);
         if (b) {
-            c.bm_cur[wi] = 0u;
+            g_sh.bm_cur[wi] = 0u;
             act = b & ~large & ~again;
         }
     }
@@ -564,7 +644,7 @@ __device__ __forceinline__ void scan_words(const GraphArgs<OffT> &a, int64_t g, 
         const uint32_t ex = __shfl_sync(0xffffffffu, excl, owner);
         const uint32_t word = __shfl_sync(0xffffffffu, act, owner);
         int32_t u = 0;
-        if (ok) u = (int32_t)((g * c.gw + owner) * 32 + __fns(word, 0, (int)(t - ex) + 1));
+        if (ok) u = (int32_t)((g * g_sh.gw + owner) * 32 + __fns(word, 0, (int)(t - ex) + 1));
         expand_group<OffT, UNIT>(a, ok, u, c);
     }
 }
@@ -604,7 +684,7 @@ __device__ __forceinline__ void pull_batch(const GraphArgs<OffT> &a, bool ok, in
         }
         uint32_t fw[kPullUnroll];
 #pragma unroll
-        for (int j = 0; j < kPullUnroll; j++) fw[j] = in[j] ? __ldcg(c.bm_cur + (u[j] >> 5)) : 0u;
+        for (int j = 0; j < kPullUnroll; j++) fw[j] = in[j] ? __ldcg(g_sh.bm_cur + (u[j] >> 5)) : 0u;
 #pragma unroll
         for (int j = 0; j < kPullUnroll; j++) {
             if (in[j] && !found) {
@@ -636,7 +716,7 @@ __device__ __forceinline__ void pull_batch(const GraphArgs<OffT> &a, bool ok, in
             }
             uint32_t fw[kPullUnroll];
 #pragma unroll
-            for (int j = 0; j < kPullUnroll; j++) fw[j] = in[j] ? __ldcg(c.bm_cur + (u[j] >> 5)) : 0u;
+            for (int j = 0; j < kPullUnroll; j++) fw[j] = in[j] ? __ldcg(g_sh.bm_cur + (u[j] >> 5)) : 0u;
 #pragma unroll
             for (int j = 0; j < kPullUnroll; j++) {
                 const uint32_t bal = __ballot_sync(0xffffffffu, in[j] && ((fw[j] >> (u[j] & 31)) & 1u));
@@ -677,7 +757,7 @@ __device__ __forceinline__ void pull_words(const GraphArgs<OffT> &a, int64_t g, 
     const int64_t w0 = g * kGroupWords;
     const int q = lane_id();
     uint32_t unv = 0;  // lane q < kGroupWords: vertices of word w0 + q not reached yet
-    if (c.vis_valid) {
+    if (g_sh.vis_valid) {
         if (q < kGroupWords && w0 + q < a.nwords) {
             unv = ~__ldcg(a.vis + w0 + q);
             const int64_t left = (int64_t)a.n - (w0 + q) * 32;
@@ -728,9 +808,9 @@ __device__ __forceinline__ void pull_words(const GraphArgs<OffT> &a, int64_t g, 
     if (q < kGroupWords && w0 + q < a.nwords) {
         const int64_t wi = w0 + q;
         const uint32_t f = s_found[q];
-        if (!c.vis_valid || f) a.vis[wi] = ~unv | f;
+        if (!g_sh.vis_valid || f) a.vis[wi] = ~unv | f;
         const uint32_t nb = f & __ldg(&a.cls[wi].x);
-        if (nb) c.bm_next[wi] = nb;
+        if (nb) g_sh.bm_next[wi] = nb;
     }
     __syncwarp();
 }
@@ -740,7 +820,9 @@ __device__ __forceinline__ void pull_words(const GraphArgs<OffT> &a, int64_t g, 
 struct BlockFlush {
     uint32_t ns[16], nc[16];
     uint32_t base_s, base_c, marked;
-    unsigned long long edges;
+    unsigned long long edges;        // arcs examined by the CTA in this sweep
+    unsigned long long total_edges;  // ... in the run
+    unsigned long long items, adv;   // run statistics of the CTA
 };
 
 template <typename OffT>
@@ -749,13 +831,13 @@ __device__ __forceinline__ void flush_sweep(const GraphArgs<OffT> &a, SweepCtx &
     const uint32_t nk = c.k + 1, nx = nk % 3;
     const uint32_t m = warp_sum(c.marked);
     c.marked = 0;
-    const unsigned long long de = warp_sum(c.edges - c.edges_flushed);
-    c.edges_flushed = c.edges;
+    const uint32_t de = warp_sum(c.edges);
+    c.edges = 0;
     if (lane_id() == 0) {
         bf->ns[wid] = c.st_ns;
         bf->nc[wid] = c.st_nc;
         if (m) atomicAdd(&bf->marked, m);
-        if (de) atomicAdd(&bf->edges, de);
+        if (de) atomicAdd(&bf->edges, (unsigned long long)de);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -773,13 +855,14 @@ __device__ __forceinline__ void flush_sweep(const GraphArgs<OffT> &a, SweepCtx &
         if (bf->marked) atomicAdd(&a.h->n_small[nx], bf->marked);
         bf->marked = 0;
         if (bf->edges) atomicAdd(&a.h->sweep_edges[c.k & 1], bf->edges);
+        bf->total_edges += bf->edges;
         bf->edges = 0;
     }
     __syncthreads();
-    int32_t *ls = a.small[nk & 1] + bf->base_s + bf->ns[wid];
-    for (uint32_t i = lane_id(); i < c.st_ns; i += 32) ls[i] = c.st_small[i];
-    int2 *lc = a.chunk[nk & 1] + bf->base_c + bf->nc[wid];
-    for (uint32_t i = lane_id(); i < c.st_nc; i += 32) lc[i] = c.st_chunk[i];
+    int32_t *ls = pick2(a.small, nk) + bf->base_s + bf->ns[wid];
+    for (uint32_t i = lane_id(); i < c.st_ns; i += 32) ls[i] = g_stage_small[warp_in_cta()][i];
+    int2 *lc = pick2(a.chunk, nk) + bf->base_c + bf->nc[wid];
+    for (uint32_t i = lane_id(); i < c.st_nc; i += 32) lc[i] = g_stage_chunk[warp_in_cta()][i];
     c.st_ns = 0;
     c.st_nc = 0;
 }
@@ -791,9 +874,6 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
     __shared__ BlockFlush s_flush;
     __shared__ uint32_t s_work[2];
     __shared__ uint32_t s_cwork[2];
-    __shared__ int32_t s_stage_small[16][kStageSmall];
-    __shared__ int2 s_stage_chunk[16][kStageChunk];
-    __shared__ int32_t s_lq[16][kLocalQ];
     WsHeader *h = a.h;
     const long long t0 = globaltimer_ns();
     const long long deadline = t0 + a.deadline_ns;
@@ -810,6 +890,9 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
     if (threadIdx.x == 0) {
         s_flush.marked = 0;
         s_flush.edges = 0;
+        s_flush.total_edges = 0;
+        s_flush.items = 0;
+        s_flush.adv = 0;
         s_work[0] = 0;
         s_work[1] = 0;
         s_cwork[0] = 0;
@@ -817,29 +900,44 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
     }
 
     SweepCtx c;
-    c.mode = a.mode;
-    c.delta = a.delta;
-    c.cfg = a.cfg;
-    if (a.use_dev_sched && *(volatile int32_t *)&h->sched_valid) {
-        c.mode = *(volatile int32_t *)&h->sched_mode;
-        c.delta = *(volatile uint32_t *)&h->sched_delta;
-        c.cfg = *(volatile int32_t *)&h->sched_cfg;
-        if (c.mode < 0 || c.mode > 2) c.mode = LLP_MODE_AUTO;
-        if (c.cfg < 1 || c.cfg > LLP_BLOCK_CFGS) c.cfg = 2;
-        if (UNIT) c.delta = kInf;
-    }
-    int32_t gw_req = a.group_words;
-    if (a.use_dev_sched && *(volatile int32_t *)&h->sched_valid) gw_req = *(volatile int32_t *)&h->sched_gw;
+    // the schedule of this run: from the arguments, or chosen on the device (learned)
+    int32_t small_max;
     {
-        const BlockCfg bcfg = block_cfg_of(c.cfg);
-        c.small_max = bcfg.small_max;
-        c.chunk_edges = bcfg.chunk;
-        // dense items: the widest group that still gives every warp about three items
-        c.gw = gw_req;
-        if (c.gw != 1 && c.gw != 2 && c.gw != 4 && c.gw != kGroupWords) {
-            const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-            c.gw = kGroupWords;
-            while (c.gw > 1 && (int64_t)a.nwords / c.gw < 3 * warps) c.gw >>= 1;
+        const bool dev = a.use_dev_sched && *(volatile int32_t *)&h->sched_valid;
+        int32_t mode = a.mode, cfg = a.cfg, gw = a.group_words;
+        uint32_t delta = a.delta;
+        if (dev) {
+            mode = *(volatile int32_t *)&h->sched_mode;
+            delta = *(volatile uint32_t *)&h->sched_delta;
+            cfg = *(volatile int32_t *)&h->sched_cfg;
+            gw = *(volatile int32_t *)&h->sched_gw;
+            if (mode < 0 || mode > 2) mode = LLP_MODE_AUTO;
+            if (cfg < 1 || cfg > LLP_BLOCK_CFGS) cfg = 2;
+            if (UNIT) delta = kInf;
+        }
+        const BlockCfg bcfg = block_cfg_of(cfg);
+        small_max = bcfg.small_max;
+        if (threadIdx.x == 0) {
+            // dense items: the widest group that still gives every warp about three items
+            if (gw != 1 && gw != 2 && gw != 4 && gw != kGroupWords) {
+                const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+                gw = kGroupWords;
+                while (gw > 1 && (int64_t)a.nwords / gw < 3 * warps) gw >>= 1;
+            }
+            g_sh.mode = mode;
+            g_sh.cfg = cfg;
+            g_sh.delta = delta;
+            g_sh.small_max = bcfg.small_max;
+            g_sh.chunk_edges = bcfg.chunk;
+            g_sh.gw = gw;
+            g_sh.chain = (dev ? *(volatile int32_t *)&h->sched_chain : a.local_chain);
+            g_sh.fa = 0;
+            g_sh.bucket_hi = (delta == kInf) ? (1ull << 40) : (unsigned long long)delta;
+            g_sh.fixed_lo = 0;
+            g_sh.pull = false;
+            g_sh.vis_valid = false;
+            g_sh.advance_bucket = false;
+            g_sh.bm_next = a.bm[1];  // warm seeding appends to sweep 1
         }
     }
 
@@ -847,34 +945,30 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
     // a learned run had the state initialised by its prologue (for the default block
     // configuration); only the large bits change when the chosen one differs
     if (!a.pre_init) {
-        const SweepInit<OffT> ini{a.n, a.source, a.warm, (uint32_t)c.small_max, a.off, a.dist, a.cls,
+        const SweepInit<OffT> ini{a.n, a.source, a.warm, (uint32_t)small_max, a.off, a.dist, a.cls,
                                   a.bm[0], a.bm[1], a.bm[2], a.fixed};
         sweep_init(ini, gwarp, nwarps);
-    } else if (c.small_max != a.small_max) {
+    } else if (small_max != a.small_max) {
         for (int64_t base = gwarp * 32; base < a.n; base += nwarps * 32) {
             const int64_t v = base + lane_id();
             const uint32_t deg = v < a.n ? (uint32_t)(__ldg(a.off + v + 1) - __ldg(a.off + v)) : 0u;
-            const uint32_t large = __ballot_sync(0xffffffffu, deg > (uint32_t)c.small_max);
+            const uint32_t large = __ballot_sync(0xffffffffu, deg > (uint32_t)small_max);
             if (lane_id() == 0) a.cls[base >> 5].y = large;
         }
     }
     if (gtid == 0) {
         h->t_start = t0;
-        h->mode_used = c.mode;
-        h->delta_used = c.delta;
-        h->block_cfg_used = c.cfg;
+        h->mode_used = g_sh.mode;
+        h->delta_used = g_sh.delta;
+        h->block_cfg_used = g_sh.cfg;
         for (int i = 0; i < 3; i++) h->far_min[i] = kInf;
         h->list_ok[1] = 1;
     }
     bool alive = grid_barrier(h, phase, deadline);
-    c.st_small = s_stage_small[threadIdx.x >> 5];
-    c.st_chunk = s_stage_chunk[threadIdx.x >> 5];
-    c.lq = s_lq[threadIdx.x >> 5];
     if (a.warm && alive) {
         // initial_states_to_process of a warm start: every seed with a finite d and
         // out-arcs enters B_1 (deduplicated) and the worklists of sweep 1
         c.k = 0;
-        c.bm_next = a.bm[1];
         for (int64_t base = gwarp * 32; base < a.n_seeds; base += nwarps * 32) {
             const int64_t i = base + lane_id();
             int32_t u = i < a.n_seeds ? a.seeds[i] : -1;
@@ -902,11 +996,11 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
         const uint32_t src_deg = (uint32_t)(__ldg(a.off + a.source + 1) - __ldg(a.off + a.source));
         if (src_deg > 0) {
             a.bm[1][a.source >> 5] = 1u << (a.source & 31);
-            if (src_deg <= (uint32_t)c.small_max) {
+            if (src_deg <= (uint32_t)g_sh.small_max) {
                 a.small[1][0] = a.source;
                 h->n_small[1] = 1;
             } else {
-                const uint32_t nch = (src_deg + c.chunk_edges - 1) / c.chunk_edges;
+                const uint32_t nch = (src_deg + g_sh.chunk_edges - 1) / g_sh.chunk_edges;
                 for (uint32_t q = 0; q < nch; q++) a.chunk[1][q] = make_int2(a.source, (int)q);
                 h->n_chunk[1] = nch;
             }
@@ -914,33 +1008,50 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
     }
     if (alive) alive = grid_barrier(h, phase, deadline);
 
-    c.chain = a.local_chain;
-    if (a.use_dev_sched && *(volatile int32_t *)&h->sched_valid) c.chain = *(volatile int32_t *)&h->sched_chain;
-    if (gtid == 0) h->scratch[8] = (uint32_t)c.chain;
+    if (gtid == 0) h->scratch[8] = (uint32_t)g_sh.chain;
     c.k = 1;
-    c.fa = 0;
-    c.bucket_hi = (c.delta == kInf) ? (1ull << 40) : (unsigned long long)c.delta;
-    c.fixed_lo = 0;
     uint32_t dense_sweeps = 0, pull_sweeps = 0;
-    bool prev_pull = false;
     while (alive) {
         const uint32_t k = c.k;
-        c.bm_cur = a.bm[k % 3];
-        c.bm_next = a.bm[(k + 1) % 3];
-        if (prev_pull) {
+        // thread 0 sets up the sweep for the CTA: it reads the worklist sizes once (the
+        // same header words read by every warp of the grid queue up at one L2 slice)
+        if (threadIdx.x == 0) {
+            if (g_sh.advance_bucket) {
+                g_sh.fixed_lo = g_sh.bucket_hi;  // the bucket just emptied: everything below it is final
+                g_sh.bucket_hi = g_sh.next_hi;
+                g_sh.fa += 1;
+                g_sh.advance_bucket = false;
+            }
+            g_sh.prev_pull = g_sh.pull;
+            g_sh.vis_valid = g_sh.pull;  // push sweeps reach vertices without recording them in vis
+            g_sh.bm_cur = pick3(a.bm, k);
+            g_sh.bm_next = pick3(a.bm, k + 1);
+            const uint32_t ns = ld_relaxed_u32(&h->n_small[k % 3]);
+            const uint32_t nc = ld_relaxed_u32(&h->n_chunk[k % 3]);
+            g_sh.ns = ns;
+            g_sh.nc = nc;
+            g_sh.dense = ld_relaxed_u32(&h->list_ok[k % 3]) == 0;
+            const unsigned long long arcs = (unsigned long long)ns * (unsigned long long)g_sh.small_max / 2 +
+                                            (unsigned long long)nc * (unsigned long long)g_sh.chunk_edges;
+            bool dn = g_sh.mode == LLP_MODE_DENSE || (g_sh.mode == LLP_MODE_AUTO && arcs > a.dense_arcs);
+            if (ns + nc == 0) dn = false;
+            const bool pl = PULL && UNIT && g_sh.chain == 0 && ns + nc > 0 && arcs > a.pull_arcs;
+            g_sh.pull = pl;
+            g_sh.dense_next = dn && !pl;  // a pull sweep appends every vertex it reaches
+            if (ns + nc == 0) {
+                g_sh.nf = ld_relaxed_u32(&h->n_far[g_sh.fa % 3]);
+                g_sh.fmin = ld_relaxed_u32(&h->far_min[g_sh.fa % 3]);
+            }
+        }
+        __syncthreads();
+        const uint32_t ns = g_sh.ns;
+        const uint32_t nc = g_sh.nc;
+        const bool dense = g_sh.dense;
+        if (g_sh.prev_pull) {
             // B_{k-1} was read, not consumed, by the pull sweep k-1; it becomes B_{k+2}
-            uint32_t *spare = a.bm[(k + 2) % 3];
+            uint32_t *spare = pick3(a.bm, k + 2);
             for (int64_t wi = gtid; wi < a.nwords; wi += gthreads) spare[wi] = 0u;
         }
-        const uint32_t ns = *(volatile uint32_t *)&h->n_small[k % 3];
-        const uint32_t nc = *(volatile uint32_t *)&h->n_chunk[k % 3];
-        const bool dense = *(volatile uint32_t *)&h->list_ok[k % 3] == 0;
-        const unsigned long long arcs = (unsigned long long)ns * (unsigned long long)c.small_max / 2 +
-                                        (unsigned long long)nc * (unsigned long long)c.chunk_edges;
-        c.dense_next = c.mode == LLP_MODE_DENSE || (c.mode == LLP_MODE_AUTO && arcs > a.dense_arcs);
-        if (ns + nc == 0) c.dense_next = false;
-        c.pull = PULL && UNIT && c.chain == 0 && ns + nc > 0 && arcs > a.pull_arcs;
-        if (c.pull) c.dense_next = false;  // a pull sweep appends every vertex it reaches
         if (threadIdx.x == 0) {  // used after the next grid barrier
             s_work[(k + 1) & 1] = 0;
             s_cwork[(k + 1) & 1] = 0;
@@ -951,7 +1062,7 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
             h->n_chunk[r] = 0;
             h->work[r] = 0;
             h->list_ok[r] = 0;
-            h->list_ok[(k + 1) % 3] = c.dense_next ? 0u : 1u;
+            h->list_ok[(k + 1) % 3] = g_sh.dense_next ? 0u : 1u;
             if (k - 1 < kSweepLogCap)
                 sweep_log(h)[k - 1] = SweepRec{(uint32_t)(globaltimer_ns() - t0), ns, nc,
                                                (dense ? 1u : 0u) | (ns + nc == 0 ? 2u : 0u)};
@@ -965,19 +1076,18 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
         }
         if (ns + nc == 0) {
             // near worklist empty: move to the next non-empty bucket, or stop
-            const uint32_t nf_raw = *(volatile uint32_t *)&h->n_far[c.fa % 3];
-            const uint32_t nf = min(nf_raw, a.far_cap);
+            const uint32_t nf = min(g_sh.nf, a.far_cap);
             if (nf == 0) break;
-            const unsigned long long fmin = *(volatile uint32_t *)&h->far_min[c.fa % 3];
-            const unsigned long long dl = c.delta;
+            const unsigned long long fmin = g_sh.fmin;
+            const unsigned long long dl = g_sh.delta;
             unsigned long long nh = (fmin / dl + 1ull) * dl;
-            if (nh < c.bucket_hi + dl) nh = c.bucket_hi + dl;
+            if (nh < g_sh.bucket_hi + dl) nh = g_sh.bucket_hi + dl;
             if (gtid == 0) {
-                h->n_far[(c.fa + 2) % 3] = 0;
-                h->far_min[(c.fa + 2) % 3] = kInf;
+                h->n_far[(g_sh.fa + 2) % 3] = 0;
+                h->far_min[(g_sh.fa + 2) % 3] = kInf;
                 h->aux += 1;
             }
-            const int2 *fl = a.far[c.fa & 1];
+            const int2 *fl = pick2(a.far, g_sh.fa);
             for (int64_t base = gwarp * 32; base < nf; base += nwarps * 32) {
                 const int64_t i = base + lane_id();
                 const bool ok = i < nf;
@@ -989,11 +1099,11 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
                 }
                 bool to_near[1] = {live && (unsigned long long)(uint32_t)e.y < nh};
                 const bool keep = live && !to_near[0];
-                const uint32_t slot = warp_append_slot(keep, &h->n_far[(c.fa + 1) % 3]);
+                const uint32_t slot = warp_append_slot(keep, &h->n_far[(g_sh.fa + 1) % 3]);
                 if (keep) {
                     if (slot < a.far_cap) {
-                        a.far[(c.fa + 1) & 1][slot] = e;
-                        atomicMin(&h->far_min[(c.fa + 1) % 3], (uint32_t)e.y);
+                        pick2(a.far, g_sh.fa + 1)[slot] = e;
+                        atomicMin(&h->far_min[(g_sh.fa + 1) % 3], (uint32_t)e.y);
                     } else {
                         to_near[0] = true;
                     }
@@ -1002,13 +1112,14 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
                 const uint32_t cl[1] = {ok ? class_of(a, e.x) : 0u};
                 push_near(a, to_near, vv, cl, c);
             }
-            c.fixed_lo = c.bucket_hi;  // the bucket just emptied: everything below it is final
-            c.bucket_hi = nh;
-            c.fa += 1;
-        } else if (PULL && c.pull) {
+            if (threadIdx.x == 0) {  // taken at the start of the next sweep
+                g_sh.next_hi = nh;
+                g_sh.advance_bucket = true;
+            }
+        } else if (PULL && g_sh.pull) {
             pull_sweeps++;
             const uint32_t ngroups = (uint32_t)(((int64_t)a.nwords + kGroupWords - 1) / kGroupWords);
-            uint32_t *s_found = reinterpret_cast<uint32_t *>(s_lq[threadIdx.x >> 5]);  // no local chain in pull runs
+            uint32_t *s_found = reinterpret_cast<uint32_t *>(g_lq[warp_in_cta()]);  // no local chain in pull runs
             for (;;) {
                 uint32_t j = 0;
                 if (lane_id() == 0) j = atomicAdd(&s_work[k & 1], 1u);
@@ -1022,8 +1133,8 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
             // chunks: CTA b owns items b, b + G, b + 2G, ... (G = grid size; a hub's chunks
             // are consecutive in the list, so they spread over CTAs) and its warps take them
             // in turn from a shared counter (costs vary: skipped, partial and full chunks)
-            const int2 *cl = a.chunk[k & 1];
-            c.chain_on = c.chain > 0;
+            const int2 *cl = pick2(a.chunk, k);
+            c.chain_on = g_sh.chain > 0;
             auto chunk_loop = [&]() {
                 for (;;) {
                     uint32_t j = 0;
@@ -1037,9 +1148,9 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
             // vertex groups (their cost varies): CTA b owns groups b, b + G, b + 2G, ...
             // (G = grid size) and its warps take them in turn from a shared counter
             auto group_loop = [&]() {
-                const uint32_t ngroups = dense ? (uint32_t)(((int64_t)a.nwords + c.gw - 1) / c.gw)
+                const uint32_t ngroups = dense ? (uint32_t)(((int64_t)a.nwords + g_sh.gw - 1) / g_sh.gw)
                                                : (uint32_t)(((uint64_t)ns + 31) / 32);
-                const int32_t *sl = a.small[k & 1];
+                const int32_t *sl = pick2(a.small, k);
                 for (;;) {
                     uint32_t j = 0;
                     if (lane_id() == 0) j = atomicAdd(&s_work[k & 1], 1u);
@@ -1054,14 +1165,17 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
                         const int64_t i = (int64_t)g * 32 + lane_id();
                         bool ok = i < ns;
                         int32_t u = ok ? sl[i] : 0;
-                        if (ok) red_and(c.bm_cur + (u >> 5), ~(1u << (u & 31)));
-                        expand_group<OffT, UNIT>(a, ok, u, c, c.bm_next);  // advanced again: next sweep
+                        if (ok) red_and(g_sh.bm_cur + (u >> 5), ~(1u << (u & 31)));
+                        expand_group<OffT, UNIT>(a, ok, u, c, g_sh.bm_next);  // advanced again: next sweep
                         if (c.chain_on) drain_local<OffT, UNIT>(a, c);
                     }
                 }
             };
             chunk_loop();
             group_loop();
+#if LLP_DEFER
+            if (c.pend_n) drain_pending(a, c);
+#endif
             c.chain_on = false;
         }
 #ifdef LLP_SWEEP_TRACE
@@ -1076,26 +1190,28 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
             a.trace[((k - 1) * 1024 + blockIdx.x) * 2 + 1] = (uint32_t)(globaltimer_ns() - t0);
         }
 #endif
-        prev_pull = c.pull;
-        c.vis_valid = c.pull;  // push sweeps reach vertices without recording them in vis
-        c.pull = false;
         alive = grid_barrier(h, phase, deadline);
         c.k += 1;
     }
 
     // ---- final_solution: dist[] already holds G
 
-    // ---- statistics (one atomic per warp)
-    const unsigned long long it_s = warp_sum(c.items), ed_s = warp_sum(c.edges), ad_s = warp_sum(c.adv);
+    // ---- statistics (one atomic per CTA and counter)
+    const uint32_t it_s = warp_sum(c.items), ad_s = warp_sum(c.adv);
     if (lane_id() == 0) {
-        atomicAdd(&h->items, it_s);
-        atomicAdd(&h->edges, ed_s);
-        atomicAdd(&h->advances, ad_s);
+        atomicAdd(&s_flush.items, (unsigned long long)it_s);
+        atomicAdd(&s_flush.adv, (unsigned long long)ad_s);
     }
     if (gtid == 0) {
         h->sweeps = (int32_t)c.k;
         h->dense_sweeps = (int32_t)dense_sweeps;
         h->scratch[7] = pull_sweeps;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&h->items, s_flush.items);
+        atomicAdd(&h->edges, s_flush.total_edges);
+        atomicAdd(&h->advances, s_flush.adv);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
