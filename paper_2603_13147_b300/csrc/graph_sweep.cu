@@ -89,6 +89,10 @@ constexpr int kPullUnroll = 4;  // in-arcs per lane and round (pull sweeps)
 #define LLP_DENSE_GROUP_WORDS 8
 #endif
 constexpr int kGroupWords = LLP_DENSE_GROUP_WORDS;  // bitmap words per dense-sweep item
+// A hub source whose 256-arc chunks would not give every warp one is seeded as
+// chunks of kFineChunk arcs (chunk index | kFineFlag in the list entry).
+constexpr int32_t kFineChunk = 64;
+constexpr int32_t kFineFlag = 1 << 30;
 
 template <typename OffT>
 struct GraphArgs {
@@ -173,6 +177,7 @@ struct SweepShared {
     bool prev_pull;                // the previous sweep ran over the in-arcs
     bool vis_valid;                // a.vis holds every vertex reached so far
     bool advance_bucket;           // the next sweep starts the bucket next_hi
+    bool fine_src;                 // the source is seeded as chunks of kFineChunk arcs
 };
 
 
@@ -554,9 +559,11 @@ __device__ __forceinline__ void drain_local(const GraphArgs<OffT> &a, SweepCtx &
 template <typename OffT, bool UNIT>
 __device__ __forceinline__ void chunk_body(const GraphArgs<OffT> &a, int32_t y, uint32_t du, OffT b0, OffT e0,
                                            SweepCtx &c) {
-    const OffT beg = b0 + (OffT)y * (OffT)g_sh.chunk_edges;
-    const OffT end = min(e0, beg + (OffT)g_sh.chunk_edges);
-    c.items += (lane_id() == 0 && y == 0);
+    const OffT size = (y & kFineFlag) ? (OffT)kFineChunk : (OffT)g_sh.chunk_edges;
+    const int32_t yy = y & ~kFineFlag;
+    const OffT beg = b0 + (OffT)yy * size;
+    const OffT end = min(e0, beg + size);
+    c.items += (lane_id() == 0 && yy == 0);
     c.edges += (lane_id() == 0) ? (uint32_t)(end - beg) : 0u;
     for (OffT base = beg; base < end; base += 32 * kUnroll) {
         bool ok[kUnroll], ovf[kUnroll];
@@ -593,7 +600,7 @@ __device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item
         du = __ldcg(a.dist + u);
         b0 = __ldg(a.off + u);
         e0 = __ldg(a.off + u + 1);
-        if (item.y == 0) red_and(g_sh.bm_cur + (u >> 5), ~bit);
+        if ((item.y & ~kFineFlag) == 0) red_and(g_sh.bm_cur + (u >> 5), ~bit);
     }
     nxt = __shfl_sync(0xffffffffu, nxt, 0);
     if (nxt & bit) return;  // warp-uniform
@@ -611,7 +618,8 @@ __device__ __forceinline__ void expand_chunk(const GraphArgs<OffT> &a, int2 item
 // are cleared.
 template <typename OffT, bool UNIT>
 __device__ __forceinline__ void scan_words(const GraphArgs<OffT> &a, int64_t g, SweepCtx &c) {
-    const int64_t wi = g * g_sh.gw + lane_id();
+    const int64_t w0 = g * g_sh.gw;
+    const int64_t wi = w0 + lane_id();
     uint32_t act = 0;
     if (lane_id() < g_sh.gw && wi < a.nwords) {
         const uint32_t b = __ldcg(g_sh.bm_cur + wi);
@@ -644,7 +652,7 @@ __device__ __forceinline__ void scan_words(const GraphArgs<OffT> &a, int64_t g, 
         const uint32_t ex = __shfl_sync(0xffffffffu, excl, owner);
         const uint32_t word = __shfl_sync(0xffffffffu, act, owner);
         int32_t u = 0;
-        if (ok) u = (int32_t)((g * g_sh.gw + owner) * 32 + __fns(word, 0, (int)(t - ex) + 1));
+        if (ok) u = (int32_t)((w0 + owner) * 32 + __fns(word, 0, (int)(t - ex) + 1));
         expand_group<OffT, UNIT>(a, ok, u, c);
     }
 }
@@ -938,6 +946,14 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
             g_sh.vis_valid = false;
             g_sh.advance_bucket = false;
             g_sh.bm_next = a.bm[1];  // warm seeding appends to sweep 1
+            if (!a.warm) {
+                const uint32_t src_deg = (uint32_t)(__ldg(a.off + a.source + 1) - __ldg(a.off + a.source));
+                const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+                g_sh.fine_src = src_deg > (uint32_t)bcfg.small_max &&
+                                (int64_t)((src_deg + bcfg.chunk - 1) / bcfg.chunk) < warps;
+            } else {
+                g_sh.fine_src = false;
+            }
         }
     }
 
@@ -992,17 +1008,23 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
         }
         flush_sweep(a, c, &s_flush);
     }
-    if (gtid == 0 && alive && !a.warm) {
+    if (blockIdx.x == 0 && alive && !a.warm) {
+        // initial_states_to_process: the source (CTA 0 writes its list entries)
         const uint32_t src_deg = (uint32_t)(__ldg(a.off + a.source + 1) - __ldg(a.off + a.source));
         if (src_deg > 0) {
-            a.bm[1][a.source >> 5] = 1u << (a.source & 31);
+            if (threadIdx.x == 0) a.bm[1][a.source >> 5] = 1u << (a.source & 31);
             if (src_deg <= (uint32_t)g_sh.small_max) {
-                a.small[1][0] = a.source;
-                h->n_small[1] = 1;
+                if (threadIdx.x == 0) {
+                    a.small[1][0] = a.source;
+                    h->n_small[1] = 1;
+                }
             } else {
-                const uint32_t nch = (src_deg + g_sh.chunk_edges - 1) / g_sh.chunk_edges;
-                for (uint32_t q = 0; q < nch; q++) a.chunk[1][q] = make_int2(a.source, (int)q);
-                h->n_chunk[1] = nch;
+                const uint32_t csize = g_sh.fine_src ? (uint32_t)kFineChunk : (uint32_t)g_sh.chunk_edges;
+                const uint32_t nch = (src_deg + csize - 1) / csize;
+                const int32_t flag = g_sh.fine_src ? kFineFlag : 0;
+                for (uint32_t q = threadIdx.x; q < nch; q += blockDim.x)
+                    a.chunk[1][q] = make_int2(a.source, (int)q | flag);
+                if (threadIdx.x == 0) h->n_chunk[1] = nch;
             }
         }
     }
@@ -1031,8 +1053,10 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
             g_sh.ns = ns;
             g_sh.nc = nc;
             g_sh.dense = ld_relaxed_u32(&h->list_ok[k % 3]) == 0;
+            const unsigned long long csize = (k == 1 && g_sh.fine_src) ? (unsigned long long)kFineChunk
+                                                                       : (unsigned long long)g_sh.chunk_edges;
             const unsigned long long arcs = (unsigned long long)ns * (unsigned long long)g_sh.small_max / 2 +
-                                            (unsigned long long)nc * (unsigned long long)g_sh.chunk_edges;
+                                            (unsigned long long)nc * csize;
             bool dn = g_sh.mode == LLP_MODE_DENSE || (g_sh.mode == LLP_MODE_AUTO && arcs > a.dense_arcs);
             if (ns + nc == 0) dn = false;
             const bool pl = PULL && UNIT && g_sh.chain == 0 && ns + nc > 0 && arcs > a.pull_arcs;
