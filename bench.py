@@ -592,7 +592,9 @@ def bench_batched(llp, dev, stream, div=1, cpu=True):
     # plain engine: one single-instance call per instance (sampled per family)
     wk = torch.from_numpy(knap["w"]).to(dev)
     vk = torch.from_numpy(knap["v"]).to(dev)
-    wsk = llp.workspace(llp.lib().llp_knapsack_workspace_size(ctypes.c_int32(0), ctypes.c_int32(65536)) + (1 << 20), dev)
+    n_max = int(np.diff(knap["item_off"]).max())
+    w_max = int(knap["capacity"].max())
+    wsk = llp.workspace(llp.lib().llp_knapsack_workspace_size(ctypes.c_int32(n_max), ctypes.c_int32(w_max)), dev)
     best = torch.empty(1, dtype=torch.int32, device=dev)
     kidx = np.arange(0, knap["count"], 16)
 

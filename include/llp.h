@@ -297,7 +297,13 @@ llp_status_t llp_stable_marriage(int32_t n, const int32_t *men_pref, const int32
  * forbidden iff G[k,c] < max(G[k-1,c], v_k + G[k-1,c-w_k]); advance raises it
  * to that bound.  best[0] = G[n, capacity]; final_row (optional, int32[capacity+1])
  * = G[n, 0..capacity].  Requires w[i] >= 1, v[i] >= 0, sum(v) < 2^31,
- * 0 <= capacity <= 2^26. */
+ * 0 <= capacity <= 2^26.  Large instances run as a wavefront over capacity
+ * slices whose rows pass through a ring of up to 256 rows of (capacity + 1)
+ * 8-byte words in the workspace (cleared by the call), so the workspace size
+ * grows with both arguments; a workspace sized for (n, capacity) serves every
+ * instance with at most n items and at most that capacity.  A wait of the
+ * wavefront that passes the schedule's deadline ends the call with
+ * LLP_ERR_TIMEOUT in the status word. */
 size_t llp_knapsack_workspace_size(int32_t n_items, int32_t capacity);
 llp_status_t llp_knapsack(int32_t n_items, const int32_t *w, const int32_t *v, int32_t capacity, int32_t *best,
                           int32_t *final_row, const llp_sched_t *sched, void *ws, size_t ws_bytes, void *stream);

@@ -8,16 +8,20 @@
 // barrier between items (knapsack_cta).  The row lives in shared memory when
 // it fits (W+1 <= 56K cells), otherwise in the workspace (L1/L2 resident).
 //
-// Large single instances run on a thread-block cluster instead (knapsack_cluster):
-// CTA r of a cluster of CL CTAs (one per SM) owns capacities [r*S, (r+1)*S) of
-// the row, double-buffered in its shared memory; a cell's lower neighbours
-// G[k-1, c - w] that another CTA owns are read from that CTA's shared memory
-// (distributed shared memory), and one cluster barrier separates passes.  Each
-// pass applies K items at once: G[k+K-1, c] = max over the subsets T of the K
-// items that fit of G[k-1, c - w(T)] + v(T) (the recurrence unrolled K times,
-// all terms read from the row before the pass), so the dependent chain of
-// barriers is n/K long (K = 2: each pass costs about as many remote loads as
-// cells x 2^K, so 2 items per pass measured fastest, 1 and 3 close behind).
+// Large single instances run as a wavefront over capacity slices instead
+// (knapsack_wave, below): one CTA per slice on every SM, no grid-wide barrier
+// per item; a CTA waits only for the cells of lower slices it reads.
+//
+// The thread-block cluster kernel (knapsack_cluster, opt-in with block
+// configuration 3): CTA r of a cluster of CL CTAs (one per SM) owns capacities
+// [r*S, (r+1)*S) of the row, double-buffered in its shared memory; a cell's
+// lower neighbours G[k-1, c - w] that another CTA owns are read from that CTA's
+// shared memory (distributed shared memory), and one cluster barrier separates
+// passes.  Each pass applies K items at once: G[k+K-1, c] = max over the
+// subsets T of the K items that fit of G[k-1, c - w(T)] + v(T) (the recurrence
+// unrolled K times, all terms read from the row before the pass), so the
+// dependent chain of barriers is n/K long (K = 2 measured fastest).
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "llp_common.cuh"
@@ -177,6 +181,263 @@ __global__ void __launch_bounds__(kClusterThreads) knapsack_cluster(int32_t n, c
     cluster.sync();  // no CTA leaves while another may still read its row
 }
 
+// ---------------------------------------------------------------------------
+// Wavefront over capacity slices (knapsack_wave): CTA s of P co-resident CTAs owns
+// the capacities [s*S, (s+1)*S) and keeps its part of G[k] and G[k+1] in shared
+// memory.  Row k+1 depends on row k at c and c - w_k, and c - w_k < c, so a CTA
+// only ever waits for CTAs below it: no grid-wide barrier per item.  Every cell
+// of G[k] is also written to a ring of R rows in global memory (L2-resident) as
+// one 64-bit word, value | k << 32; a CTA that needs G[k][x] of a lower slice
+// takes the ring word only when its tag is k (the data carry their own
+// readiness: no fence, no flag on the dependency path) and loads the words of
+// kWaveF items ahead of use.  Each CTA publishes the number of items it has done
+// (relaxed store, per block of kWaveF items); before overwriting the ring slot of
+// G[j], a CTA waits until every CTA that may read it (those within the largest
+// item weight above it) has done item j.  Every wait is bounded by the call's
+// deadline; a CTA that gives up raises the header's abort flag, which the others
+// check while waiting.
+constexpr int kWaveThreads = 512;
+#ifndef LLP_WAVE_F
+#define LLP_WAVE_F 4
+#endif
+constexpr int kWaveF = LLP_WAVE_F;  // items per block (ring loads in flight, progress published per block)
+constexpr int kWaveWin = 1024;
+  // items whose parameters are staged in shared memory at a time
+
+__device__ __forceinline__ unsigned long long ld_ring(const unsigned long long *p) {
+    unsigned long long x;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(x) : "l"(p));
+    return x;
+}
+__device__ __forceinline__ void st_ring(unsigned long long *p, unsigned long long x) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(x) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t x) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
+}
+
+// Gives up a wait: timeout status and the abort flag (first caller), or a
+// deadline check every 64 spins.  Returns true when the wait must end.
+__device__ __forceinline__ bool wave_give_up(WsHeader *h, uint32_t spins, long long deadline) {
+    if ((spins & 63u) != 63u) return false;
+    if (ld_relaxed_u32(&h->abort_flag)) return true;
+    if (globaltimer_ns() > deadline) {
+        set_status(h, LLP_ERR_TIMEOUT);
+        atomicExch(&h->abort_flag, 1u);
+        return true;
+    }
+    return false;
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kWaveThreads, 1)
+    knapsack_wave(int32_t n, const int32_t *w, const int32_t *v, int32_t W, int32_t S, int32_t R,
+                  unsigned long long *ring, uint32_t *prog, int32_t *best, int32_t *final_row, WsHeader *h,
+                  long long deadline_ns) {
+    extern __shared__ int32_t sbuf[];
+    __shared__ int2 s_item[kWaveWin];  // (weight, value) of the items of the current window
+    __shared__ int s_abort;
+    __shared__ int32_t s_wmax;
+    __shared__ long long s_known;  // a lower bound of the readers' published item counts
+    const int32_t s = blockIdx.x, P = gridDim.x, tid = threadIdx.x, T = blockDim.x;
+    const long long t0 = globaltimer_ns();
+    const long long deadline = t0 + deadline_ns;
+    const int32_t lo = s * S, hi = min(lo + S, W + 1);
+    const size_t row_len = (size_t)W + 1;
+    if (cta_sum_i32(n, v) > 0x7FFFFFFFll) {  // every CTA computes it: same answer
+        if (s == 0 && tid == 0) set_status(h, LLP_ERR_OVERFLOW);
+        return;
+    }
+    // largest weight of an item that fits (its reads reach that far below a cell)
+    if (tid == 0) {
+        s_wmax = 0;
+        s_abort = 0;
+        s_known = 0;
+    }
+    __syncthreads();
+    int32_t wm = 0;
+    for (int32_t i = tid; i < n; i += T) {
+        const int32_t a = __ldg(w + i);
+        if (a <= W && a > wm) wm = a;
+    }
+    atomicMax(&s_wmax, wm);
+    int32_t *prev = sbuf, *cur = sbuf + S;
+    for (int32_t i = tid; i < S; i += T) prev[i] = 0;  // G[0] = 0
+    // the CTAs that read this CTA's cells: those whose slice starts within s_wmax above it
+    __syncthreads();
+    const int32_t reach = min(P - 1, s + 1 + (s_wmax + S - 1) / S);
+    // ring words of the lower slices for one block of items (ahead of use: the next block's
+    // words are loaded while the current block runs)
+    auto prefetch = [&](int32_t kb0, unsigned long long (&pf)[kWaveF][Q]) {
+#pragma unroll
+        for (int j = 0; j < kWaveF; j++) {
+            const int32_t k = kb0 + j;
+            const int32_t wj = k < n ? s_item[k % kWaveWin].x : W + 1;
+#pragma unroll
+            for (int q = 0; q < Q; q++) {
+                const int32_t c = lo + tid + q * T;
+                const int32_t x = c - wj;
+                const bool rd = c < hi && wj <= c && x < lo && k >= 1;
+                pf[j][q] = rd ? ld_ring(ring + (size_t)(k & (R - 1)) * row_len + x) : 0ull;
+            }
+        }
+    };
+    unsigned long long pf_cur[kWaveF][Q], pf_nxt[kWaveF][Q];
+    for (int32_t k0 = 0; k0 < n; k0 += kWaveF) {
+        const int32_t kb = min(kWaveF, n - k0);
+        if (k0 % kWaveWin == 0) {
+            // next window of item parameters (an item outside the problem statement never fits)
+            __syncthreads();
+            for (int32_t i = tid; i < kWaveWin && k0 + i < n; i += T) {
+                int32_t a = __ldg(w + k0 + i), b = __ldg(v + k0 + i);
+                if (a < 1 || b < 0) {
+                    set_status(h, LLP_ERR_INVALID_ARG);
+                    a = W + 1;
+                    b = 0;
+                }
+                s_item[i] = make_int2(a > W ? W + 1 : a, b);
+            }
+            __syncthreads();
+            prefetch(k0, pf_nxt);
+        }
+#pragma unroll
+        for (int j = 0; j < kWaveF; j++)
+#pragma unroll
+            for (int q = 0; q < Q; q++) pf_cur[j][q] = pf_nxt[j][q];
+        if ((k0 + kWaveF) % kWaveWin != 0 && k0 + kWaveF < n) prefetch(k0 + kWaveF, pf_nxt);
+        // this block writes G[k0+1 .. k0+kb] over G[k0+1-R .. k0+kb-R]; a CTA reads G[j] during item j,
+        // so every reader must have done items up to k0+kb-R (published count >= k0+kb-R+1)
+        const int64_t need = (int64_t)k0 + kb - R + 1;
+        if (need > s_known) {  // uniform: s_known changes only between CTA barriers
+            __syncthreads();
+            if (tid < 32) {
+                for (uint32_t spins = 0;; spins++) {
+                    uint32_t mn = 0xFFFFFFFFu;
+                    for (int32_t c2 = s + 1 + tid; c2 <= reach; c2 += 32)
+                        mn = min(mn, ld_relaxed_u32(prog + (size_t)c2 * 32));
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                    if ((int64_t)mn >= need) {
+                        if (tid == 0) s_known = (long long)mn;
+                        break;
+                    }
+                    if (__any_sync(0xffffffffu, wave_give_up(h, spins, deadline))) {
+                        if (tid == 0) s_abort = 1;
+                        break;
+                    }
+                }
+            }
+            __syncthreads();  // no warp writes the block's ring rows before the readers are done
+            if (s_abort) break;
+        }
+        bool quit = false;
+#pragma unroll
+        for (int j = 0; j < kWaveF; j++) {
+            if (j >= kb) break;
+            const int32_t k = k0 + j;
+            const int2 it = s_item[k % kWaveWin];
+            const int32_t wj = it.x, vj = it.y;
+            unsigned long long *dst = ring + (size_t)((k + 1) & (R - 1)) * row_len;
+#pragma unroll
+            for (int q = 0; q < Q; q++) {
+                const int32_t c = lo + tid + q * T;
+                if (c < hi) {
+                    int32_t g = prev[c - lo];
+                    if (wj <= c) {
+                        const int32_t x = c - wj;
+                        int32_t lower;
+                        if (x >= lo) {
+                            lower = prev[x - lo];
+                        } else if (k == 0) {
+                            lower = 0;
+                        } else {
+                            unsigned long long e = pf_cur[j][q];
+                            const unsigned long long *src = ring + (size_t)(k & (R - 1)) * row_len + x;
+                            for (uint32_t spins = 0; (uint32_t)(e >> 32) != (uint32_t)k; spins++) {
+                                if (wave_give_up(h, spins, deadline)) {
+                                    s_abort = 1;
+                                    break;
+                                }
+                                e = ld_ring(src);
+                            }
+                            lower = (int32_t)(uint32_t)e;
+                        }
+                        const int32_t cand = lower + vj;
+                        g = cand > g ? cand : g;
+                    }
+                    cur[c - lo] = g;
+                    st_ring(dst + c, ((unsigned long long)(uint32_t)(k + 1) << 32) | (uint32_t)g);
+                }
+            }
+            __syncthreads();
+            int32_t *t = prev;
+            prev = cur;
+            cur = t;
+            if (s_abort) {
+                quit = true;
+                break;
+            }
+        }
+        if (quit) break;
+        if (tid == 0) st_relaxed_u32(prog + (size_t)s * 32, (uint32_t)(k0 + kb));
+    }
+    if (s_abort) return;
+    if (final_row)
+        for (int32_t c = lo + tid; c < hi; c += T) final_row[c] = prev[c - lo];
+    if (W >= lo && W < hi && tid == 0) best[0] = prev[W - lo];
+    if (s == 0 && tid == 0) {
+        h->t_start = t0;
+        h->t_end = globaltimer_ns();
+        h->sweeps = n;
+        h->items = (unsigned long long)n;
+        h->edges = (unsigned long long)n * (unsigned long long)(W + 1);
+    }
+}
+
+// Slices, cells per thread and ring rows of the wavefront for capacity W (cl = 0:
+// W too large for Q <= 8 cells per thread on the co-resident CTAs).
+struct WavePlan {
+    int P = 0, Q = 0;
+    int32_t S = 0, R = 0;
+    size_t smem = 0;
+};
+
+#ifndef LLP_WAVE_Q
+#define LLP_WAVE_Q 1
+#endif
+#ifndef LLP_WAVE_R
+#define LLP_WAVE_R 256
+#endif
+
+WavePlan plan_wave(int32_t n, int32_t W) {
+    WavePlan pl;
+    const DeviceInfo di = device_info();
+    if (di.sms <= 0) return pl;
+    const int64_t cells = (int64_t)W + 1;
+    // about LLP_WAVE_Q cells per thread; more only when the SMs run out
+    int Q = LLP_WAVE_Q;
+    int64_t P = (cells + (int64_t)kWaveThreads * Q - 1) / ((int64_t)kWaveThreads * Q);
+    while (P > di.sms && Q < 8) {
+        Q *= 2;
+        P = (cells + (int64_t)kWaveThreads * Q - 1) / ((int64_t)kWaveThreads * Q);
+    }
+    if (P > di.sms || P < 2) return pl;
+    pl.P = (int)P;
+    pl.Q = Q;
+    pl.S = (int32_t)((cells + P - 1) / P);
+    // a power of two (slots by mask), at least two blocks and one row more, at most what the items need
+    int32_t R = 1;
+    while (R < 2 * kWaveF + 2 || (R < LLP_WAVE_R && R < n + 1)) R *= 2;
+    pl.R = R;
+    pl.smem = (size_t)pl.S * 2 * 4;
+    return pl;
+}
+
+size_t wave_workspace_bytes(const WavePlan &pl, int32_t W) {
+    if (pl.P == 0) return 0;
+    return align_up((size_t)pl.R * ((size_t)W + 1) * 8, 256) + (size_t)pl.P * 128;
+}
+
 // Cluster size and cells per CTA for capacity W, or 0 when the row does not fit
 // the cluster's shared memory (the single-CTA kernel then runs it).
 struct ClusterPlan {
@@ -234,8 +495,9 @@ extern "C" {
 size_t llp_knapsack_workspace_size(int32_t n_items, int32_t capacity) {
     if (n_items < 0 || capacity < 0) return 0;
     size_t b = llp::kHeaderBytes;
-    if (capacity + 1 > llp::kSmemCells) b += llp::align_up((size_t)(capacity + 1) * 4, 256);
-    return b;
+    size_t extra = capacity + 1 > llp::kSmemCells ? llp::align_up((size_t)(capacity + 1) * 4, 256) : 0;
+    extra = std::max(extra, llp::wave_workspace_bytes(llp::plan_wave(n_items, capacity), capacity));
+    return b + extra;
 }
 
 llp_status_t llp_knapsack(int32_t n_items, const int32_t *w, const int32_t *v, int32_t capacity, int32_t *best,
@@ -251,6 +513,36 @@ llp_status_t llp_knapsack(int32_t n_items, const int32_t *w, const int32_t *v, i
     // instances with more than a few thousand cell updates per item take a cluster
     const bool big = (int64_t)n_items * (int64_t)(capacity + 1) >= (1ll << 22) && capacity >= 4096 &&
                      (!sched || sched->block_cfg != 1);
+    const bool wave = big && (!sched || sched->block_cfg != 3);
+    if (wave) {
+        const WavePlan pl = plan_wave(n_items, capacity);
+        if (pl.P > 0) {
+            unsigned long long *ring = (unsigned long long *)((char *)ws + kHeaderBytes);
+            const size_t ring_bytes = (size_t)pl.R * ((size_t)capacity + 1) * 8;
+            uint32_t *prog = (uint32_t *)((char *)ws + kHeaderBytes + align_up(ring_bytes, 256));
+            // tags 0 never match a row read (rows 1..n): stale words of an earlier call are cleared
+            LLP_CUDA_TRY(cudaMemsetAsync(ring, 0, ring_bytes, st));
+            LLP_CUDA_TRY(cudaMemsetAsync(prog, 0, (size_t)pl.P * 128, st));
+            long long dl = deadline_from(sched);
+            int32_t S = pl.S, R = pl.R;
+            void *args[] = {&n_items, (void *)&w, (void *)&v, &capacity, &S, &R, &ring, &prog, &best, &final_row,
+                            &ws, &dl};
+            const void *fn = pl.Q == 1 ? (const void *)knapsack_wave<1>
+                           : pl.Q == 2 ? (const void *)knapsack_wave<2>
+                           : pl.Q == 4 ? (const void *)knapsack_wave<4> : (const void *)knapsack_wave<8>;
+            if (pl.smem > 48 * 1024)
+                LLP_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+            // the CTAs wait for one another: all P must be co-resident, else the cluster kernel runs it
+            int per_sm = 0;
+            LLP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kWaveThreads, pl.smem));
+            if ((int64_t)per_sm * device_info().sms >= pl.P) {
+                int grid = 0;
+                rc = launch_cooperative(fn, kWaveThreads, pl.smem, pl.P, args, st, &grid);
+                if (rc != LLP_OK) return rc;
+                return grid == pl.P ? LLP_OK : LLP_ERR_CUDA;
+            }
+        }
+    }
     if (big) {
         const ClusterPlan pl = plan_cluster(capacity);
         if (pl.cl > 0) {

@@ -88,11 +88,15 @@ def test_knapsack(llp, n, W, seed):
 
 
 @pytest.mark.parametrize("n,W,seed,cfg", [(2048, 65536, 5, 1), (1000, 30000, 8, 0), (1001, 65536, 9, 0),
-                                          (2000, 200000, 10, 0), (4096, 4096, 11, 0), (3, 100000, 12, 0)])
-def test_knapsack_cluster_and_single_cta(llp, n, W, seed, cfg):
-    """Large instances run on a thread-block cluster (rows in distributed shared memory, three
-    items per pass: ragged item counts leave a partial last pass); block_cfg 1 forces the one-CTA
-    kernel on the same instance."""
+                                          (2000, 200000, 10, 0), (4096, 4096, 11, 0), (3, 100000, 12, 0),
+                                          (2048, 65536, 5, 3), (1001, 65536, 9, 3), (2000, 200000, 10, 3),
+                                          (8000, 65536, 14, 0), (4099, 5000, 15, 0), (1500, 1000000, 16, 0)])
+def test_knapsack_wavefront_cluster_and_single_cta(llp, n, W, seed, cfg):
+    """Large instances run as a wavefront over capacity slices (one CTA per slice, rows exchanged
+    through a tagged ring in global memory: ragged item counts leave a partial last block, more
+    items than ring rows wrap it, a large capacity takes several cells per thread); block_cfg 3
+    runs the thread-block cluster kernel (rows in distributed shared memory, two items per pass)
+    and block_cfg 1 the one-CTA kernel on the same instance."""
     w, v = synth.knapsack(n, W, seed=seed)
     best, row, ws = llp.knapsack(T(w), T(v), W, sched=llp.make_sched(block_cfg=cfg))
     assert llp.get_status(ws)["status"] == 0
@@ -101,8 +105,8 @@ def test_knapsack_cluster_and_single_cta(llp, n, W, seed, cfg):
     assert (row.cpu().numpy() == rrow).all()
 
 
-def test_knapsack_cluster_invalid_item_reported(llp):
-    """An item outside the problem statement (weight 0) is skipped and reported on the cluster path."""
+def test_knapsack_wave_invalid_item_reported(llp):
+    """An item outside the problem statement (weight 0) is skipped and reported on the wavefront path."""
     w, v = synth.knapsack(2048, 65536, seed=13)
     w[100] = 0
     best, row, ws = llp.knapsack(T(w), T(v), 65536)
