@@ -196,7 +196,10 @@ __global__ void __launch_bounds__(kClusterThreads) knapsack_cluster(int32_t n, c
 // item weight above it) has done item j.  Every wait is bounded by the call's
 // deadline; a CTA that gives up raises the header's abort flag, which the others
 // check while waiting.
-constexpr int kWaveThreads = 512;
+#ifndef LLP_WAVE_T
+#define LLP_WAVE_T 512
+#endif
+constexpr int kWaveThreads = LLP_WAVE_T;
 #ifndef LLP_WAVE_F
 #define LLP_WAVE_F 4
 #endif
