@@ -11,6 +11,10 @@
 // counts the pairs each advance adds.  Stops after a sweep that adds nothing.
 #include "llp_common.cuh"
 
+#ifndef LLP_READ_ONCE
+#define LLP_READ_ONCE 1
+#endif
+
 namespace llp {
 namespace {
 
@@ -128,7 +132,7 @@ __global__ void __launch_bounds__(512) closure_kernel(ClosureArgs<OffT> a) {
         if (gtid == 0) h->scratch[1 + ((k + 1) & 1)] = 0;
         alive = grid_barrier(h, phase, deadline);
         if (!alive) break;
-        const uint32_t any = *(volatile uint32_t *)&h->scratch[1 + (k & 1)];
+        const uint32_t any = LLP_READ_ONCE ? cta_read_once(&h->scratch[1 + (k & 1)]) : *(volatile uint32_t *)&h->scratch[1 + (k & 1)];
         k++;
         if (!any) break;
         alive = grid_barrier(h, phase, deadline);  // everyone read `any` before it is reset

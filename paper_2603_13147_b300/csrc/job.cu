@@ -11,7 +11,12 @@
 // job.  Jobs left unfixed mean a cycle: LLP_ERR_INFEASIBLE.
 #include "llp_common.cuh"
 
+#ifndef LLP_JOB_STAGE
+#define LLP_JOB_STAGE 1
+#endif
+
 namespace llp {
+constexpr uint32_t kJobStage = 4096;  // ready jobs a CTA stages per sweep before spilling
 namespace {
 
 template <typename OffT>
@@ -31,6 +36,11 @@ struct JobArgs {
 template <typename OffT>
 __global__ void __launch_bounds__(512) job_sweep_kernel(JobArgs<OffT> a) {
     WsHeader *h = a.h;
+#if LLP_JOB_STAGE
+    __shared__ int32_t s_ready[kJobStage];
+    __shared__ uint32_t s_nready, s_base;
+    if (threadIdx.x == 0) s_nready = 0;
+#endif
     const long long t0 = globaltimer_ns();
     const long long deadline = t0 + a.deadline_ns;
     uint32_t phase = 0;
@@ -66,7 +76,7 @@ __global__ void __launch_bounds__(512) job_sweep_kernel(JobArgs<OffT> a) {
     }
     uint32_t k = 0;
     while (alive) {
-        const uint32_t cnt = *(volatile uint32_t *)&h->n_small[k % 3];
+        const uint32_t cnt = cta_read_once(&h->n_small[k % 3]);
         if (gtid == 0) h->n_small[(k + 2) % 3] = 0;
         if (cnt == 0) break;
         const int32_t *cur = a.list[k & 1];
@@ -121,10 +131,38 @@ __global__ void __launch_bounds__(512) job_sweep_kernel(JobArgs<OffT> a) {
                     atomicMax(a.maxp + s, co);
                     ready = atomicSub(a.remaining + s, 1) == 1;
                 }
+#if LLP_JOB_STAGE
+                // ready jobs are staged in the CTA's shared buffer; a full buffer spills to the list
+                const uint32_t mask = __ballot_sync(0xffffffffu, ready);
+                if (mask) {
+                    uint32_t at = 0;
+                    if (lane_id() == 0) at = atomicAdd(&s_nready, (uint32_t)__popc(mask));
+                    at = __shfl_sync(0xffffffffu, at, 0);
+                    const uint32_t my = at + __popc(mask & lanemask_lt());
+                    // every buffer position below kJobStage is written by exactly one lane; the
+                    // lanes past the buffer's end go straight to the list
+                    if (ready && my < kJobStage) s_ready[my] = s;
+                    if (at + __popc(mask) > kJobStage) {
+                        const bool spill = ready && my >= kJobStage;
+                        const uint32_t slot = warp_append_slot(spill, ncount);
+                        if (spill) nxt[slot] = s;
+                    }
+                }
+#else
                 const uint32_t slot = warp_append_slot(ready, ncount);
                 if (ready) nxt[slot] = s;
+#endif
             }
         }
+#if LLP_JOB_STAGE
+        // the CTA's staged ready jobs: one reservation in the next list
+        __syncthreads();
+        const uint32_t nst = min(s_nready, kJobStage);
+        if (threadIdx.x == 0) s_base = nst ? atomicAdd(ncount, nst) : 0u;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < nst; i += blockDim.x) nxt[s_base + i] = s_ready[i];
+        if (threadIdx.x == 0) s_nready = 0;  // read again only after the grid barrier
+#endif
         alive = grid_barrier(h, phase, deadline);
         k++;
     }

@@ -151,6 +151,20 @@ __device__ __forceinline__ bool grid_barrier(WsHeader *h, uint32_t &phase, long 
     return s_ok != 0;
 }
 
+// A word every thread of a grid needs at the same point (a worklist size, a
+// change flag): one thread per CTA reads it and the CTA shares it through shared
+// memory, instead of every warp of the grid reading the same L2 line (those
+// requests queue at one L2 slice).  CTA-collective.
+template <typename T>
+__device__ __forceinline__ T cta_read_once(const T *p) {
+    __shared__ T s_v;
+    if (threadIdx.x == 0) s_v = *(volatile const T *)p;
+    __syncthreads();
+    const T v = s_v;
+    __syncthreads();  // every thread has the value before a later call overwrites it
+    return v;
+}
+
 // Warp-aggregated append of one element per participating lane.  All 32 lanes
 // of the warp must call it (converged); lanes with `want` false contribute
 // nothing.  Returns the slot index for lanes with want, else undefined.

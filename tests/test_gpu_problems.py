@@ -155,6 +155,26 @@ def test_job_int64_offsets(llp):
     assert (c.cpu().numpy() == oracle.job_schedule(dur, g["offsets"], g["indices"])).all()
 
 
+@pytest.mark.parametrize("fan", [5000, 100000])
+def test_job_wide_ready_sets(llp, fan):
+    """A job with `fan` successors, each with one more successor: one warp makes all of them
+    ready in one sweep, more than a CTA stages in shared memory (the rest spill to the list)."""
+    rng = np.random.default_rng(fan)
+    n = 1 + 2 * fan
+    src = np.concatenate([np.zeros(fan, np.int64), np.arange(1, fan + 1)])
+    dst = np.concatenate([np.arange(1, fan + 1), np.arange(fan + 1, n)])
+    offsets = np.zeros(n + 1, np.int64)
+    np.add.at(offsets, src + 1, 1)
+    offsets = np.cumsum(offsets)
+    indices = dst[np.argsort(src, kind="stable")].astype(np.int32)
+    g = dict(n=n, m=len(indices), offsets=offsets, indices=indices, weights=None)
+    dur = rng.integers(1, 101, n).astype(np.int32)
+    c, ws = llp.job_schedule(job_dev(llp, g), T(dur))
+    st = llp.get_status(ws)
+    assert st["status"] == 0, st
+    assert (c.cpu().numpy() == oracle.job_schedule(dur, offsets, indices)).all()
+
+
 def test_job_cycle_is_infeasible(llp):
     g = dict(n=3, m=3, offsets=np.array([0, 1, 2, 3], np.int64), indices=np.array([1, 2, 0], np.int32), weights=None)
     _, ws = llp.job_schedule(job_dev(llp, g), T(np.ones(3, np.int32)))
