@@ -212,8 +212,11 @@ __device__ __forceinline__ unsigned long long ld_ring(const unsigned long long *
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(x) : "l"(p));
     return x;
 }
+// No "memory" clobber: the shared-memory work of the item may move across the store (the
+// ring words carry their own tags; volatile asm keeps the ring and progress accesses in order,
+// and the CTA barrier orders the shared row).
 __device__ __forceinline__ void st_ring(unsigned long long *p, unsigned long long x) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(x) : "memory");
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(x));
 }
 __device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t x) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
