@@ -34,7 +34,7 @@ WORKLOAD = "rmat22_ef16_sssp"
 # R-MAT scale 20 (dram__bytes_read.sum + dram__bytes_write.sum of one launch), valid
 # only for the kernel source it was taken from (sha256 prefix of graph_sweep.cu +
 # llp_common.cuh).
-TRAFFIC_CAPTURE = {"src_sha": "ee3bc1eecc7303cc", "bytes_per_alg_byte": 1.2746}
+TRAFFIC_CAPTURE = {"src_sha": "c76e1eb7563feea6", "bytes_per_alg_byte": 1.2747}
 
 
 def kernel_src_sha():
