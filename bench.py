@@ -54,28 +54,80 @@ def dist_env():
 
 
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons while running."""
+    """Samples the SM clock, its maximum and the clock-event (throttle) reasons while
+    running: through NVML in this process every ~1 ms (the timed regions are a few
+    milliseconds long), else through nvidia-smi every 200 ms.  Only samples taken
+    between __enter__ and __exit__ are kept."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits (nvml.h, nvmlClocksEventReason*)
+    REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                   "hw_thermal_slowdown": 0x40}
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
-        self.rows = []
+        self.rows = []  # (sm_mhz, max_mhz, {reason: bool})
+        self.source = None
         self._stop = threading.Event()
         self._t = None
+        self._nvml = None
+        try:
+            self._nvml = self._nvml_open()
+            self.source = "nvml"
+        except Exception:
+            self._nvml = None
+            self.source = "nvidia-smi"
+
+    def _nvml_open(self):
+        """NVML through its C API (libnvidia-ml, shipped with the driver): (library, handle)
+        of CUDA device `gpu`, found through the visible-device list (index or UUID)."""
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        hd = ctypes.c_void_p()
+        ids = [x.strip() for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+        if ids and self.gpu < len(ids) and not ids[self.gpu].isdigit():
+            rc = nv.nvmlDeviceGetHandleByUUID(ids[self.gpu].encode(), ctypes.byref(hd))
+        else:
+            idx = int(ids[self.gpu]) if ids and self.gpu < len(ids) else self.gpu
+            rc = nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(idx), ctypes.byref(hd))
+        if rc != 0:
+            raise RuntimeError("no NVML handle")
+        reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        return nv, hd, reasons
+
+    def _sample_nvml(self):
+        nv, hd, reasons = self._nvml
+        sm, mx, bits = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        if (nv.nvmlDeviceGetClockInfo(hd, 1, ctypes.byref(sm)) != 0 or  # 1 = NVML_CLOCK_SM
+                nv.nvmlDeviceGetMaxClockInfo(hd, 1, ctypes.byref(mx)) != 0 or reasons(hd, ctypes.byref(bits)) != 0):
+            return
+        self.rows.append((float(sm.value), float(mx.value),
+                          {k: bool(bits.value & b) for k, b in self.REASON_BITS.items()}))
+
+    def _sample_smi(self):
+        out = subprocess.run(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                              "-i", str(self.gpu)], capture_output=True, text=True, timeout=5).stdout
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            r = [x.strip() for x in line.split(",")]
+            if len(r) >= 9 and r[1].replace('.', '', 1).isdigit() and r[2].replace('.', '', 1).isdigit():
+                self.rows.append((float(r[1]), float(r[2]),
+                                  {nm: r[5 + i].lower().startswith("active") for i, nm in enumerate(names)}))
 
     def _run(self):
         while not self._stop.is_set():
             try:
-                out = subprocess.run(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                      "-i", str(self.gpu)], capture_output=True, text=True, timeout=5).stdout
-                for line in out.strip().splitlines():
-                    self.rows.append([x.strip() for x in line.split(",")])
+                if self._nvml:
+                    self._sample_nvml()
+                else:
+                    self._sample_smi()
             except Exception:
                 pass
-            self._stop.wait(0.2)
+            self._stop.wait(0.001 if self._nvml else 0.2)
 
     def __enter__(self):
         self._t = threading.Thread(target=self._run, daemon=True)
@@ -88,17 +140,11 @@ class ClockSampler:
             self._t.join(timeout=10)
 
     def summary(self):
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace('.', '', 1).isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace('.', '', 1).isdigit()]
-        reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
-            if len(r) >= 9:
-                for i, nm in enumerate(names):
-                    if r[5 + i].lower().startswith("active"):
-                        reasons.add(nm)
+        sm = [r[0] for r in self.rows]
+        mx = [r[1] for r in self.rows]
+        reasons = sorted({k for r in self.rows for k, on in r[2].items() if on})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(self.rows), "source": self.source}
 
 
 def combine_ranks(ms_local: float, units_local: int, device=None):
@@ -238,23 +284,22 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     sched = None
 
-    # warm-up (also checks the device status)
-    for _ in range(args.warmup):
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # warm-up (also checks the device status), directly followed by the timed steps so
+    # that the GPU does not idle in between
+    for i in range(args.warmup):
+        flush.fill_(i & 0xFF)
         llp.sssp(dg, s, out=dist_t, sched=sched, ws=ws)
     st = llp.get_status(ws)
     if st["status"] != 0:
         raise RuntimeError(f"llp_sssp device status {st}")
-    d_host = llp.as_u32(dist_t)
-    mr, nr = reached_arcs(g, d_host)
 
     # timed region: per-step CUDA events on the launching stream, L2 flushed between steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
-    clocks = ClockSampler(dev.index if dev.index is not None else 0)
     with clocks:
-        time.sleep(0.3)
         t_wall0 = time.perf_counter()
         for i in range(args.steps):
             flush.fill_(i & 0xFF)
@@ -266,6 +311,10 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = float(np.mean(step_ms))
     st = llp.get_status(ws)
+    if st["status"] != 0:
+        raise RuntimeError(f"llp_sssp device status {st}")
+    d_host = llp.as_u32(dist_t)
+    mr, nr = reached_arcs(g, d_host)
     slog = llp.sweep_log(ws)
     ms, units = combine_ranks(ms, mr, device=dev)
     value = units / (ms * 1e-3) / 1e9
@@ -419,6 +468,8 @@ def run_gpu(args):
         "sweep_stats": {"sweeps": st["sweeps"], "edges_scanned": st["edges"], "advances": st["advances"],
                         "dense_sweeps": st["dense_sweeps"], "edges_per_reached_arc": st["edges"] / max(mr, 1),
                         "device_loop_ms": st["elapsed_ns"] / 1e6,
+                        "step_ms_min_median_max": [float(np.min(step_ms)), float(np.median(step_ms)),
+                                                   float(np.max(step_ms))],
                         "per_sweep": [[round(int(r[0]) / 1e6, 4), int(r[1]), int(r[2]), int(r[3])] for r in slog]},
         "bfs": {"gteps": bfs_mr / (bfs_ms * 1e-3) / 1e9, "ms": bfs_ms, "sweeps": bfs_st["sweeps"],
                 "edges_scanned": bfs_st["edges"], "status": bfs_st["status"],
