@@ -185,6 +185,9 @@ constexpr uint32_t kStageSmall = 128;  // entries per warp
 constexpr uint32_t kStageChunk = 128;
 constexpr uint32_t kDirectChunks = 4;  // a lane with more chunk entries reserves them directly
 constexpr uint32_t kLocalQ = 128;      // per-warp stack of the local chain
+// after a flush a warp stages at most 32 lanes x kUnroll small vertices, or 32 lanes x
+// kDirectChunks chunk entries, at once
+static_assert(kStageSmall >= 32 * kUnroll && kStageChunk >= 32 * kDirectChunks, "staging buffers too small");
 
 __shared__ SweepShared g_sh;
 __shared__ int32_t g_stage_small[16][kStageSmall];  // per warp
