@@ -34,7 +34,7 @@ WORKLOAD = "rmat22_ef16_sssp"
 # R-MAT scale 20 (dram__bytes_read.sum + dram__bytes_write.sum of one launch), valid
 # only for the kernel source it was taken from (sha256 prefix of graph_sweep.cu +
 # llp_common.cuh).
-TRAFFIC_CAPTURE = {"src_sha": "c76e1eb7563feea6", "bytes_per_alg_byte": 1.2747}
+TRAFFIC_CAPTURE = {"src_sha": "5dc3f07785ffa401", "bytes_per_alg_byte": 1.2801}
 
 
 def kernel_src_sha():
@@ -55,8 +55,8 @@ def dist_env():
 
 class ClockSampler:
     """Samples the SM clock, its maximum and the clock-event (throttle) reasons while
-    running: through NVML in this process every ~1 ms (the timed regions are a few
-    milliseconds long), else through nvidia-smi every 200 ms.  Only samples taken
+    running: through NVML in this process every ~0.2 ms plus the query time (the
+    timed regions are a few milliseconds long), else through nvidia-smi every 200 ms.  Only samples taken
     between __enter__ and __exit__ are kept."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -127,7 +127,7 @@ class ClockSampler:
                     self._sample_smi()
             except Exception:
                 pass
-            self._stop.wait(0.001 if self._nvml else 0.2)
+            self._stop.wait(0.0002 if self._nvml else 0.2)
 
     def __enter__(self):
         self._t = threading.Thread(target=self._run, daemon=True)

@@ -93,6 +93,14 @@ constexpr int kGroupWords = LLP_DENSE_GROUP_WORDS;  // bitmap words per dense-sw
 // chunks of kFineChunk arcs (chunk index | kFineFlag in the list entry).
 constexpr int32_t kFineChunk = 64;
 constexpr int32_t kFineFlag = 1 << 30;
+#ifndef LLP_CTAKE
+#define LLP_CTAKE 4
+#endif
+#ifndef LLP_CTAKE_MIN
+#define LLP_CTAKE_MIN 24
+#endif
+constexpr uint32_t kTake = LLP_CTAKE;        // chunk items per claim in wide chunk sweeps
+constexpr uint32_t kTakeMin = LLP_CTAKE_MIN;  // ... with at least this many per warp
 
 template <typename OffT>
 struct GraphArgs {
@@ -1162,14 +1170,40 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
             // in turn from a shared counter (costs vary: skipped, partial and full chunks)
             const int2 *cl = pick2(a.chunk, k);
             c.chain_on = g_sh.chain > 0;
+            // With many chunk items per warp (most of them skipped in the early sweeps of a
+            // power-law graph) a warp takes kTake of its CTA's items at once and loads their
+            // entries and "advanced again" words in parallel, one per lane; the survivors
+            // are expanded in order (and tested again, as every chunk item is).
+            const uint32_t take = (kTake > 1 && (uint64_t)nc >= (uint64_t)kTakeMin * nwarps) ? kTake : 1u;
             auto chunk_loop = [&]() {
                 for (;;) {
                     uint32_t j = 0;
-                    if (lane_id() == 0) j = atomicAdd(&s_cwork[k & 1], 1u);
+                    if (lane_id() == 0) j = atomicAdd(&s_cwork[k & 1], take);
                     j = __shfl_sync(0xffffffffu, j, 0);
-                    const uint64_t it = (uint64_t)blockIdx.x + (uint64_t)j * gridDim.x;
-                    if (it >= nc) break;
-                    expand_chunk<OffT, UNIT>(a, cl[it], c);
+                    if (take == 1) {
+                        const uint64_t it = (uint64_t)blockIdx.x + (uint64_t)j * gridDim.x;
+                        if (it >= nc) break;
+                        expand_chunk<OffT, UNIT>(a, cl[it], c);
+                        continue;
+                    }
+                    const uint64_t it = (uint64_t)blockIdx.x + (uint64_t)(j + lane_id()) * gridDim.x;
+                    const bool ok = lane_id() < take && it < nc;
+                    if (!__any_sync(0xffffffffu, ok)) break;
+                    int2 item = make_int2(0, 0);
+                    bool live = false;
+                    if (ok) {
+                        item = cl[it];
+                        const uint32_t bit = 1u << (item.x & 31);
+                        live = (__ldcg(g_sh.bm_next + (item.x >> 5)) & bit) == 0u;
+                        if ((item.y & ~kFineFlag) == 0) red_and(g_sh.bm_cur + (item.x >> 5), ~bit);
+                    }
+                    uint32_t todo = __ballot_sync(0xffffffffu, live);
+                    while (todo) {
+                        const int q = __ffs(todo) - 1;
+                        todo &= todo - 1u;
+                        const int2 iq = make_int2(__shfl_sync(0xffffffffu, item.x, q), __shfl_sync(0xffffffffu, item.y, q));
+                        expand_chunk<OffT, UNIT>(a, iq, c);
+                    }
                 }
             };
             // vertex groups (their cost varies): CTA b owns groups b, b + G, b + 2G, ...
