@@ -93,6 +93,13 @@ constexpr int kGroupWords = LLP_DENSE_GROUP_WORDS;  // bitmap words per dense-sw
 // chunks of kFineChunk arcs (chunk index | kFineFlag in the list entry).
 constexpr int32_t kFineChunk = 64;
 constexpr int32_t kFineFlag = 1 << 30;
+#ifndef LLP_MIN_GROUP
+#define LLP_MIN_GROUP 4
+#endif
+// A sparse sweep whose worklist would not give every warp a group of 32 vertices
+// takes groups of 16, 8, ... down to kMinGroup vertices (their arcs still spread
+// over the 32 lanes), so the few busy warps run shorter chains.
+constexpr uint32_t kMinGroup = LLP_MIN_GROUP;
 #ifndef LLP_CTAKE
 #define LLP_CTAKE 4
 #endif
@@ -186,6 +193,7 @@ struct SweepShared {
     bool vis_valid;                // a.vis holds every vertex reached so far
     bool advance_bucket;           // the next sweep starts the bucket next_hi
     bool fine_src;                 // the source is seeded as chunks of kFineChunk arcs
+    uint32_t gsz;                  // sparse sweep: list entries per vertex group (kMinGroup..32)
 };
 
 
@@ -1064,6 +1072,12 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
             g_sh.ns = ns;
             g_sh.nc = nc;
             g_sh.dense = ld_relaxed_u32(&h->list_ok[k % 3]) == 0;
+            {
+                const uint64_t per_warp = (uint64_t)ns / (uint64_t)nwarps;
+                uint32_t gs = 32;
+                while (gs > kMinGroup && per_warp < gs) gs >>= 1;
+                g_sh.gsz = gs;
+            }
             const unsigned long long csize = (k == 1 && g_sh.fine_src) ? (unsigned long long)kFineChunk
                                                                        : (unsigned long long)g_sh.chunk_edges;
             const unsigned long long arcs = (unsigned long long)ns * (unsigned long long)g_sh.small_max / 2 +
@@ -1209,8 +1223,9 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
             // vertex groups (their cost varies): CTA b owns groups b, b + G, b + 2G, ...
             // (G = grid size) and its warps take them in turn from a shared counter
             auto group_loop = [&]() {
+                const uint32_t gsz = g_sh.gsz;
                 const uint32_t ngroups = dense ? (uint32_t)(((int64_t)a.nwords + g_sh.gw - 1) / g_sh.gw)
-                                               : (uint32_t)(((uint64_t)ns + 31) / 32);
+                                               : (uint32_t)(((uint64_t)ns + gsz - 1) / gsz);
                 const int32_t *sl = pick2(a.small, k);
                 for (;;) {
                     uint32_t j = 0;
@@ -1223,8 +1238,8 @@ __global__ void __launch_bounds__(512, LLP_SWEEP_MIN_BLOCKS) graph_sweep_kernel(
                         scan_words<OffT, UNIT>(a, g, c);
                         if (c.chain_on) drain_local<OffT, UNIT>(a, c);
                     } else {
-                        const int64_t i = (int64_t)g * 32 + lane_id();
-                        bool ok = i < ns;
+                        const int64_t i = (int64_t)g * gsz + lane_id();
+                        bool ok = (uint32_t)lane_id() < gsz && i < ns;
                         int32_t u = ok ? sl[i] : 0;
                         if (ok) red_and(g_sh.bm_cur + (u >> 5), ~(1u << (u & 31)));
                         expand_group<OffT, UNIT>(a, ok, u, c, g_sh.bm_next);  // advanced again: next sweep
