@@ -34,7 +34,7 @@ WORKLOAD = "rmat22_ef16_sssp"
 # R-MAT scale 20 (dram__bytes_read.sum + dram__bytes_write.sum of one launch), valid
 # only for the kernel source it was taken from (sha256 prefix of graph_sweep.cu +
 # llp_common.cuh).
-TRAFFIC_CAPTURE = {"src_sha": "5f16055010016ebf", "bytes_per_alg_byte": 1.2737}
+TRAFFIC_CAPTURE = {"src_sha": "8a0ed638958a5a85", "bytes_per_alg_byte": 1.2817}
 
 
 def kernel_src_sha():

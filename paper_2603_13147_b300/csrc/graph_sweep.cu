@@ -93,6 +93,9 @@ constexpr int kGroupWords = LLP_DENSE_GROUP_WORDS;  // bitmap words per dense-sw
 // chunks of kFineChunk arcs (chunk index | kFineFlag in the list entry).
 constexpr int32_t kFineChunk = 64;
 constexpr int32_t kFineFlag = 1 << 30;
+#ifndef LLP_ONE_BUCKET_FAST
+#define LLP_ONE_BUCKET_FAST 1
+#endif
 #ifndef LLP_MIN_GROUP
 #define LLP_MIN_GROUP 4
 #endif
@@ -432,11 +435,22 @@ __device__ __forceinline__ void relax_multi(const GraphArgs<OffT> &a, const bool
             }
         }
         c.adv += improved;
-        near[j] = improved && (unsigned long long)cand[j] < g_sh.bucket_hi;
-        far[j] = improved && !near[j];
-        any_far |= far[j];
+        near[j] = improved;
     }
-    if (__any_sync(0xffffffffu, any_far)) {
+#if LLP_ONE_BUCKET_FAST
+    const bool buckets = g_sh.delta != kInf;  // one bucket: every advance is near
+#else
+    const bool buckets = true;
+#endif
+    if (buckets) {
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) {
+            far[j] = near[j] && (unsigned long long)cand[j] >= g_sh.bucket_hi;
+            near[j] = near[j] && !far[j];
+            any_far |= far[j];
+        }
+    }
+    if (buckets && __any_sync(0xffffffffu, any_far)) {
         uint32_t cnt = 0, fmin = kInf;
 #pragma unroll
         for (int j = 0; j < kUnroll; j++) {
